@@ -1,0 +1,322 @@
+/*
+ * Plain FP64 CPU oracle for the local SDDMM / SpMM computation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * include this file: it exists so that tests, the smoke check and the timed
+ * CPU baseline can compare the CUDA path against a slow, obviously correct
+ * restatement of the paper's definitions.  It shares no code, header or
+ * constant with the CUDA sources.
+ *
+ * Every routine is a direct loop over the definition, accumulating in double:
+ *   SDDMM   c_e = s_e * <a_i, b_j> for every stored e = (i, j)      (Sec. 3.2, Eq. 1)
+ *   SpMM    a_i = sum_j s_ij * b_j                                   (Sec. 3.2, Eq. 2)
+ *   SpMM^T  x_j = sum_i s_ij * y_i  (the adjoint pair of Sec. 3.2: each nonzero
+ *           takes / outputs two dense vectors)
+ * plus the bookkeeping the GPU path needs a reference for:
+ *   - a stable counting-sort transpose (CSR -> CSC with slot permutation),
+ *   - the merge-path split point of the (row ends, nonzeros) merge, by walking,
+ *   - number-format encoders / decoders written from the format definitions
+ *     (IEEE binary16, bfloat16 = top half of binary32, OCP FP8 E4M3),
+ *   - per-row E4M3 quantisation with scale = amax / 448.
+ *
+ * Build: gcc -O2 -fPIC -shared -std=c11 (no -ffast-math: the float division in
+ * the quantiser must stay the IEEE single-precision operation).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+enum { OR_F32 = 0, OR_BF16 = 1, OR_F16 = 2, OR_E4M3 = 3, OR_F64 = 4 };
+
+/* ------------------------------------------------------------------------- */
+/* Number formats, from their definitions                                    */
+/* ------------------------------------------------------------------------- */
+
+/* bfloat16: the upper 16 bits of an IEEE binary32 pattern. */
+double oracle_decode_bf16(uint32_t h)
+{
+    uint32_t bits = (h & 0xFFFFu) << 16;
+    float f;
+    memcpy(&f, &bits, sizeof f);
+    return (double)f;
+}
+
+/* IEEE binary16: 1 sign bit, 5 exponent bits (bias 15), 10 fraction bits. */
+double oracle_decode_f16(uint32_t h)
+{
+    int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (e == 0)
+        v = ldexp((double)m, -24);                 /* subnormal: m/1024 * 2^-14 */
+    else if (e == 31)
+        v = m ? NAN : INFINITY;
+    else
+        v = ldexp(1.0 + m / 1024.0, e - 15);
+    return s ? -v : v;
+}
+
+/* OCP FP8 E4M3: 1 sign bit, 4 exponent bits (bias 7), 3 mantissa bits, no
+ * infinities, S.1111.111 is NaN, largest finite magnitude 448. */
+double oracle_decode_e4m3(uint32_t q)
+{
+    int s = (q >> 7) & 1, e = (q >> 3) & 15, m = q & 7;
+    double v;
+    if (e == 15 && m == 7)
+        v = NAN;
+    else if (e == 0)
+        v = ldexp((double)m / 8.0, -6);            /* subnormal */
+    else
+        v = ldexp(1.0 + m / 8.0, e - 7);
+    return s ? -v : v;
+}
+
+typedef double (*decode_fn)(uint32_t);
+
+/* Round-to-nearest, ties-to-even, by searching the (monotone) magnitudes of
+ * the non-negative codes 0..max_code.  `beyond` is the magnitude of the first
+ * value past max_code in the unbounded-exponent format (the IEEE overflow
+ * threshold), and `overflow_code` what a magnitude rounding there becomes. */
+static uint32_t encode_nearest(double x, decode_fn dec, uint32_t max_code, double beyond,
+                               uint32_t overflow_code, uint32_t sign_bit, uint32_t nan_code)
+{
+    if (isnan(x))
+        return nan_code;
+    uint32_t sign = signbit(x) ? sign_bit : 0;
+    double ax = fabs(x);
+    /* largest code with magnitude <= ax */
+    uint32_t lo = 0, hi = max_code;
+    if (ax >= dec(max_code)) {
+        lo = max_code;
+    } else {
+        while (lo < hi) {                          /* invariant: dec(lo) <= ax */
+            uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (dec(mid) <= ax) lo = mid; else hi = mid - 1;
+        }
+    }
+    double vlo = dec(lo);
+    if (vlo == ax)
+        return sign | lo;
+    double vhi = (lo == max_code) ? beyond : dec(lo + 1);
+    double dlo = ax - vlo, dhi = vhi - ax;
+    uint32_t pick;
+    if (dlo < dhi) pick = lo;
+    else if (dhi < dlo) pick = lo + 1;
+    else pick = (lo & 1) ? lo + 1 : lo;            /* tie: even code */
+    if (pick > max_code)
+        pick = overflow_code;
+    return sign | pick;
+}
+
+uint32_t oracle_encode_bf16(float x)
+{
+    /* beyond the largest finite bf16 (0x7F7F) the next step is 2^128 -> inf */
+    return encode_nearest((double)x, oracle_decode_bf16, 0x7F7Fu, ldexp(1.0, 128),
+                          0x7F80u, 0x8000u, 0x7FC0u | (signbit(x) ? 0x8000u : 0));
+}
+
+uint32_t oracle_encode_f16(float x)
+{
+    return encode_nearest((double)x, oracle_decode_f16, 0x7BFFu, 65536.0,
+                          0x7C00u, 0x8000u, 0x7E00u | (signbit(x) ? 0x8000u : 0));
+}
+
+/* Saturating E4M3: magnitudes past 448 clamp to 448 instead of overflowing. */
+uint32_t oracle_encode_e4m3(float x)
+{
+    return encode_nearest((double)x, oracle_decode_e4m3, 0x7Eu, 480.0,
+                          0x7Eu, 0x80u, 0x7Fu | (signbit(x) ? 0x80u : 0));
+}
+
+void oracle_encode_array(int dtype, int64_t n, const float* x, void* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (dtype == OR_BF16) ((uint16_t*)out)[i] = (uint16_t)oracle_encode_bf16(x[i]);
+        else if (dtype == OR_F16) ((uint16_t*)out)[i] = (uint16_t)oracle_encode_f16(x[i]);
+        else if (dtype == OR_E4M3) ((uint8_t*)out)[i] = (uint8_t)oracle_encode_e4m3(x[i]);
+    }
+}
+
+/* Per-row E4M3 quantisation: scale_i = amax_i / 448 (1 for an all-zero row),
+ * code = E4M3_satfinite_RNE(x / scale_i), the division in binary32. */
+void oracle_quantize_e4m3_rows(int64_t M, int64_t K, const float* x, int64_t ldx,
+                               uint8_t* codes, int64_t ldq, float* scales)
+{
+    for (int64_t i = 0; i < M; ++i) {
+        float amax = 0.0f;
+        for (int64_t k = 0; k < K; ++k) {
+            float a = fabsf(x[i * ldx + k]);
+            if (a > amax) amax = a;
+        }
+        float scale = (amax > 0.0f) ? amax / 448.0f : 1.0f;
+        scales[i] = scale;
+        for (int64_t k = 0; k < K; ++k) {
+            float q = x[i * ldx + k] / scale;
+            codes[i * ldq + k] = (uint8_t)oracle_encode_e4m3(q);
+        }
+    }
+}
+
+/* One dense element, dequantised to double: value(code) * row_scale. */
+static double elem(int dtype, const void* p, int64_t idx, const float* scale, int64_t row)
+{
+    double v;
+    switch (dtype) {
+    case OR_F32:  v = (double)((const float*)p)[idx]; break;
+    case OR_BF16: v = oracle_decode_bf16(((const uint16_t*)p)[idx]); break;
+    case OR_F16:  v = oracle_decode_f16(((const uint16_t*)p)[idx]); break;
+    case OR_E4M3: v = oracle_decode_e4m3(((const uint8_t*)p)[idx]); break;
+    case OR_F64:  v = ((const double*)p)[idx]; break;
+    default:      v = NAN;
+    }
+    if (scale) v *= (double)scale[row];
+    return v;
+}
+
+static double sval(const double* vals, const double* vals2, int64_t e)
+{
+    double s = vals ? vals[e] : 1.0;
+    if (vals2) s *= vals2[e];
+    return s;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SDDMM (Eq. 1): out[e] = s_e * sum_k A[i,k] * B[j,k]                        */
+/* With abs_mode, every term is replaced by its magnitude (the condition     */
+/* denominator |s_e| * sum_k |a_ik b_jk| used by the componentwise error).   */
+/* Only rows listed in `rows` (all rows if rows == NULL) are written.        */
+/* ------------------------------------------------------------------------- */
+int oracle_sddmm(int64_t M, int64_t N, int64_t K,
+                 const int32_t* rowptr, const int32_t* colidx,
+                 const double* vals, const double* vals2, int abs_mode,
+                 int dta, const void* A, int64_t lda, const float* a_scale,
+                 int dtb, const void* B, int64_t ldb, const float* b_scale,
+                 int64_t nrows, const int64_t* rows, double* out)
+{
+    int64_t count = rows ? nrows : M;
+    for (int64_t q = 0; q < count; ++q) {
+        int64_t i = rows ? rows[q] : q;
+        if (i < 0 || i >= M) return 1;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t j = colidx[e];
+            if (j < 0 || j >= N) return 2;
+            double acc = 0.0;
+            for (int64_t k = 0; k < K; ++k) {
+                double t = elem(dta, A, i * lda + k, a_scale, i) * elem(dtb, B, j * ldb + k, b_scale, j);
+                acc += abs_mode ? fabs(t) : t;
+            }
+            double s = sval(vals, vals2, e);
+            out[e] = abs_mode ? fabs(s) * acc : s * acc;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SpMM (Eq. 2): C[q,:] = sum_{e in row i} s_e * B[j_e,:] for i = rows[q].    */
+/* ------------------------------------------------------------------------- */
+int oracle_spmm(int64_t M, int64_t N, int64_t K,
+                const int32_t* rowptr, const int32_t* colidx,
+                const double* vals, const double* vals2, int abs_mode,
+                int dtb, const void* B, int64_t ldb, const float* b_scale,
+                int64_t nrows, const int64_t* rows, double* C)
+{
+    int64_t count = rows ? nrows : M;
+    for (int64_t q = 0; q < count; ++q) {
+        int64_t i = rows ? rows[q] : q;
+        if (i < 0 || i >= M) return 1;
+        double* c = C + q * K;
+        for (int64_t k = 0; k < K; ++k) c[k] = 0.0;
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t j = colidx[e];
+            if (j < 0 || j >= N) return 2;
+            double s = sval(vals, vals2, e);
+            for (int64_t k = 0; k < K; ++k) {
+                double t = s * elem(dtb, B, j * ldb + k, b_scale, j);
+                c[k] += abs_mode ? fabs(t) : t;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SpMM with the transpose: X[q,:] = sum_{e=(i,j), j = cols[q]} s_e * Y[i,:]. */
+/* A direct scatter over the nonzeros in CSR order; it builds no transpose.  */
+/* ------------------------------------------------------------------------- */
+int oracle_spmm_t(int64_t M, int64_t N, int64_t K,
+                  const int32_t* rowptr, const int32_t* colidx,
+                  const double* vals, const double* vals2, int abs_mode,
+                  int dty, const void* Y, int64_t ldy, const float* y_scale,
+                  int64_t ncols, const int64_t* cols, double* X)
+{
+    int64_t count = cols ? ncols : N;
+    int64_t* slot = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    if (!slot) return 3;
+    for (int64_t j = 0; j < N; ++j) slot[j] = cols ? -1 : j;
+    for (int64_t q = 0; cols && q < count; ++q) {
+        if (cols[q] < 0 || cols[q] >= N) { free(slot); return 1; }
+        slot[cols[q]] = q;
+    }
+    for (int64_t q = 0; q < count * K; ++q) X[q] = 0.0;
+    for (int64_t i = 0; i < M; ++i) {
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t j = colidx[e];
+            if (j < 0 || j >= N) { free(slot); return 2; }
+            int64_t q = slot[j];
+            if (q < 0) continue;
+            double s = sval(vals, vals2, e);
+            for (int64_t k = 0; k < K; ++k) {
+                double t = s * elem(dty, Y, i * ldy + k, y_scale, i);
+                X[q * K + k] += abs_mode ? fabs(t) : t;
+            }
+        }
+    }
+    free(slot);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Transpose by a stable counting sort on the column index.                  */
+/* colptr[N+1], rowidx[nnz]: the CSC pattern; perm[p] = CSR slot of CSC slot */
+/* p.  Within a column the entries keep their CSR (row-major) order.         */
+/* ------------------------------------------------------------------------- */
+int oracle_transpose(int64_t M, int64_t N, const int32_t* rowptr, const int32_t* colidx,
+                     int32_t* colptr, int32_t* rowidx, int32_t* perm)
+{
+    int64_t nnz = rowptr[M];
+    int64_t* cursor = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    if (!cursor) return 3;
+    for (int64_t e = 0; e < nnz; ++e) {
+        if (colidx[e] < 0 || colidx[e] >= N) { free(cursor); return 2; }
+        cursor[colidx[e] + 1]++;
+    }
+    for (int64_t j = 0; j < N; ++j) cursor[j + 1] += cursor[j];
+    for (int64_t j = 0; j <= N; ++j) colptr[j] = (int32_t)cursor[j];
+    for (int64_t i = 0; i < M; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t p = cursor[colidx[e]]++;
+            rowidx[p] = (int32_t)i;
+            perm[p] = (int32_t)e;
+        }
+    free(cursor);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Merge path: walk d steps of the merge of the row-end offsets              */
+/* rowptr[1..M] with the nonzero indices 0..nnz-1.  A row end is taken first */
+/* when it is <= the next nonzero index (row r is finished once all of its   */
+/* nonzeros were consumed).  Returns (rows finished, nonzeros consumed).     */
+/* ------------------------------------------------------------------------- */
+void oracle_merge_path(int64_t M, const int32_t* rowptr, int64_t d, int64_t* r_out, int64_t* e_out)
+{
+    int64_t r = 0, e = 0, nnz = rowptr[M];
+    for (int64_t step = 0; step < d; ++step) {
+        if (r < M && rowptr[r + 1] <= e) r++;
+        else if (e < nnz) e++;
+        else r++;
+    }
+    *r_out = r;
+    *e_out = e;
+}

@@ -1,0 +1,363 @@
+"""Pins for the FP64 oracle, against things other than the oracle itself.
+
+Each check is chosen so that a plausible slip in ``oracle/oracle.c`` (a dropped
+scale, a swapped index, a transposed operand, a wrong tie rule) fails it:
+  * a hand-worked example (tests/golden/worked_3x4.json),
+  * dense brute force with numpy's FP64 matmul (Sec. 3.2, Eq. 1 and Eq. 2),
+  * the adjoint identity  sum SDDMM(S,A,B) = sum A.SpMM(S,B) = trace(A^T S B),
+  * exact integer arithmetic in pure Python on tiny inputs,
+  * special cases (identity, permutation, all-ones, K = 1, nnz = 0),
+  * library routines for the formats (torch bfloat16 / float8, numpy float16)
+    and for the transpose (scipy CSR -> CSC),
+  * an explicitly materialised merge for the merge-path split,
+  * finite differences for the closed-form gradients.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense(rowptr, colidx, vals, M, N):
+    S = np.zeros((M, N))
+    for i in range(M):
+        for e in range(rowptr[i], rowptr[i + 1]):
+            S[i, colidx[e]] += 1.0 if vals is None else vals[e]
+    return S
+
+
+def random_case(M, N, K, density, seed, empty_rows=True):
+    g = np.random.default_rng(seed)
+    mask = g.random((M, N)) < density
+    if empty_rows and M > 3:
+        mask[1] = False
+        mask[M - 1] = False
+    rows, cols = np.nonzero(mask)
+    rp, ci = synth.csr_from_coo(rows, cols, M, N)
+    vals = g.uniform(-1, 1, ci.size).astype(np.float32)
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((N, K)).astype(np.float32)
+    return rp, ci, vals, A, B
+
+
+# ----------------------------------------------------------------------------
+# Hand-worked example
+# ----------------------------------------------------------------------------
+
+def test_worked_example():
+    w = json.load(open(os.path.join(GOLDEN, "worked_3x4.json")))
+    rp = np.array(w["rowptr"], np.int32); ci = np.array(w["colidx"], np.int32)
+    vals = np.array(w["vals"]); A = np.array(w["A"], np.float32); B = np.array(w["B"], np.float32)
+    assert np.array_equal(oracle.sddmm(rp, ci, A, B, vals), w["sddmm"])
+    assert np.array_equal(oracle.spmm(rp, ci, B, vals), w["spmm"])
+    assert np.array_equal(oracle.spmm_t(rp, ci, w["N"], A, vals), w["spmm_t_of_A"])
+    assert oracle.sddmm(rp, ci, A, B, vals).sum() == w["adjoint_sum"]
+
+
+# ----------------------------------------------------------------------------
+# Brute force against dense FP64 matmul
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,N,K", [(17, 23, 1), (40, 31, 8), (33, 64, 24), (64, 40, 65)])
+def test_sddmm_dense_bruteforce(M, N, K):
+    rp, ci, vals, A, B = random_case(M, N, K, 0.2, seed=M * N + K)
+    got = oracle.sddmm(rp, ci, A, B, vals)
+    full = A.astype(np.float64) @ B.astype(np.float64).T
+    rows = np.repeat(np.arange(M), np.diff(rp))
+    want = vals.astype(np.float64) * full[rows, ci]
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("M,N,K", [(17, 23, 1), (40, 31, 8), (33, 64, 24), (64, 40, 65)])
+def test_spmm_dense_bruteforce(M, N, K):
+    rp, ci, vals, A, B = random_case(M, N, K, 0.2, seed=M + N + K)
+    got = oracle.spmm(rp, ci, B, vals)
+    want = dense(rp, ci, vals, M, N) @ B.astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    # sampled rows give the same rows
+    rows = np.array([M - 1, 0, 5])
+    np.testing.assert_allclose(oracle.spmm(rp, ci, B, vals, rows=rows), want[rows], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("M,N,K", [(17, 23, 3), (40, 31, 16)])
+def test_spmm_t_dense_bruteforce(M, N, K):
+    rp, ci, vals, A, B = random_case(M, N, K, 0.25, seed=7 * M + N)
+    Y = A
+    got = oracle.spmm_t(rp, ci, N, Y, vals)
+    want = dense(rp, ci, vals, M, N).T @ Y.astype(np.float64)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    cols = np.array([N - 1, 2, 0])
+    np.testing.assert_allclose(oracle.spmm_t(rp, ci, N, Y, vals, cols=cols), want[cols], rtol=1e-13, atol=1e-13)
+
+
+def test_absmode_is_sum_of_magnitudes():
+    M, N, K = 20, 30, 6
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=3)
+    Aa, Ba = np.abs(A.astype(np.float64)), np.abs(B.astype(np.float64))
+    rows = np.repeat(np.arange(M), np.diff(rp))
+    want = np.abs(vals) * (Aa @ Ba.T)[rows, ci]
+    np.testing.assert_allclose(oracle.sddmm(rp, ci, A, B, vals, absmode=True), want, rtol=1e-13)
+    want2 = np.abs(dense(rp, ci, vals, M, N)) @ Ba
+    np.testing.assert_allclose(oracle.spmm(rp, ci, B, vals, absmode=True), want2, rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Adjoint identity and exact integer arithmetic
+# ----------------------------------------------------------------------------
+
+def test_adjoint_identity():
+    M, N, K = 50, 70, 12
+    rp, ci, vals, A, B = random_case(M, N, K, 0.15, seed=11)
+    s1 = oracle.sddmm(rp, ci, A, B, vals).sum()
+    s2 = (A.astype(np.float64) * oracle.spmm(rp, ci, B, vals)).sum()
+    s3 = np.trace(A.astype(np.float64).T @ dense(rp, ci, vals, M, N) @ B.astype(np.float64))
+    s4 = (B.astype(np.float64) * oracle.spmm_t(rp, ci, N, A, vals)).sum()
+    assert abs(s1 - s2) < 1e-10 and abs(s1 - s3) < 1e-10 and abs(s1 - s4) < 1e-10
+
+
+def test_integer_exact_against_python_ints():
+    g = np.random.default_rng(5)
+    M, N, K = 9, 11, 5
+    mask = g.random((M, N)) < 0.4
+    rows, cols = np.nonzero(mask)
+    rp, ci = synth.csr_from_coo(rows, cols, M, N)
+    vals = g.integers(-3, 4, ci.size)
+    A = g.integers(-3, 4, (M, K)); B = g.integers(-3, 4, (N, K))
+    got = oracle.sddmm(rp, ci, A.astype(np.float32), B.astype(np.float32), vals)
+    gotC = oracle.spmm(rp, ci, B.astype(np.float32), vals)
+    for i in range(M):
+        Ci = [0] * K
+        for e in range(rp[i], rp[i + 1]):
+            j = int(ci[e])
+            dot = sum(int(A[i, k]) * int(B[j, k]) for k in range(K))
+            assert got[e] == int(vals[e]) * dot
+            for k in range(K):
+                Ci[k] += int(vals[e]) * int(B[j, k])
+        assert list(gotC[i]) == Ci
+
+
+# ----------------------------------------------------------------------------
+# Special cases
+# ----------------------------------------------------------------------------
+
+def test_identity_permutation_allones_k1_empty():
+    g = np.random.default_rng(2)
+    n, K = 16, 4
+    A = g.standard_normal((n, K)).astype(np.float32)
+    B = g.standard_normal((n, K)).astype(np.float32)
+    # S = I: SDDMM = rowwise <a_i, b_i>, SpMM = B
+    rp = np.arange(n + 1, dtype=np.int32); ci = np.arange(n, dtype=np.int32)
+    np.testing.assert_allclose(oracle.sddmm(rp, ci, A, B), (A.astype(np.float64) * B).sum(1), rtol=1e-14)
+    assert np.array_equal(oracle.spmm(rp, ci, B), B.astype(np.float64))
+    # permutation: SpMM permutes the rows of B
+    p = g.permutation(n).astype(np.int32)
+    assert np.array_equal(oracle.spmm(rp, p, B), B[p].astype(np.float64))
+    # all-ones dense S: SDDMM = the full product, SpMM = column sums of B
+    m = 5
+    rp1 = (np.arange(m + 1) * n).astype(np.int32); ci1 = np.tile(np.arange(n, dtype=np.int32), m)
+    full = A[:m].astype(np.float64) @ B.astype(np.float64).T
+    np.testing.assert_allclose(oracle.sddmm(rp1, ci1, A[:m], B), full.reshape(-1), rtol=1e-13)
+    np.testing.assert_allclose(oracle.spmm(rp1, ci1, B), np.tile(B.astype(np.float64).sum(0), (m, 1)), rtol=1e-13)
+    # K = 1: masked outer product
+    a1, b1 = A[:, :1], B[:, :1]
+    rows = np.repeat(np.arange(m), n)
+    np.testing.assert_allclose(oracle.sddmm(rp1, ci1, a1[:m], b1), a1[rows, 0].astype(np.float64) * b1[ci1, 0], rtol=1e-15)
+    # nnz = 0: SpMM writes zeros, SDDMM writes nothing
+    rp0 = np.zeros(n + 1, np.int32); ci0 = np.zeros(0, np.int32)
+    assert np.array_equal(oracle.spmm(rp0, ci0, B), np.zeros((n, K)))
+    assert oracle.sddmm(rp0, ci0, A, B).size == 0
+
+
+def test_duplicates_sum():
+    # duplicates in a row are independent entries: SpMM sums them
+    rp = np.array([0, 3], np.int32); ci = np.array([1, 1, 0], np.int32)
+    B = np.array([[1.0, 2.0], [3.0, 4.0]], np.float32)
+    vals = np.array([1.0, 2.0, -1.0])
+    assert np.array_equal(oracle.spmm(rp, ci, B, vals), [[8.0, 10.0]])
+
+
+# ----------------------------------------------------------------------------
+# Number formats
+# ----------------------------------------------------------------------------
+
+def test_e4m3_published_points():
+    pts = json.load(open(os.path.join(GOLDEN, "e4m3_points.json")))
+    for p in pts["points"]:
+        assert oracle.decode([p["code"]], "e4m3")[0] == p["value"], p
+    for c in pts["nan_codes"]:
+        assert np.isnan(oracle.decode([c], "e4m3")[0])
+
+
+def test_e4m3_table_closed_form():
+    tab = oracle.decode_table("e4m3")
+    for q in range(256):
+        s, e, m = q >> 7, (q >> 3) & 15, q & 7
+        if e == 15 and m == 7:
+            assert np.isnan(tab[q]); continue
+        v = (m / 8) * 2.0 ** -6 if e == 0 else (1 + m / 8) * 2.0 ** (e - 7)
+        assert tab[q] == (-v if s else v)
+
+
+def test_e4m3_encoder_against_torch_and_rules():
+    torch = pytest.importorskip("torch")
+    tab = oracle.decode_table("e4m3")
+    finite = [q for q in range(256) if not np.isnan(tab[q])]
+    # every representable value encodes to itself (both zeros keep their sign)
+    vals = np.array([tab[q] for q in finite], np.float32)
+    assert np.array_equal(oracle.encode(vals, "e4m3"), np.array(finite, np.uint8))
+    # random in-range values: torch's RNE float8_e4m3fn cast (a library routine)
+    g = np.random.default_rng(0)
+    x = np.concatenate([g.uniform(-448, 448, 20000), g.standard_normal(20000),
+                        g.standard_normal(5000) * 1e-3]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    assert np.array_equal(oracle.encode(x, "e4m3"), want)
+    # midpoints tie to the even code; saturation to 448 past the top
+    mid = np.float32((tab[56] + tab[57]) / 2)      # between 1.0 and 1.125 -> 1.0 (even)
+    assert oracle.encode([mid], "e4m3")[0] == 56
+    mid = np.float32((tab[57] + tab[58]) / 2)      # between 1.125 and 1.25 -> 1.25 (even)
+    assert oracle.encode([mid], "e4m3")[0] == 58
+    assert list(oracle.encode(np.array([449.0, 1e6, -500.0], np.float32), "e4m3")) == [126, 126, 254]
+
+
+def test_bf16_f16_encoders_against_libraries():
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(1)
+    x = np.concatenate([g.standard_normal(50000) * 10.0 ** g.integers(-30, 30, 50000),
+                        [0.0, -0.0, 1.0, 65504.0, 65520.0, 1e-8, 3.3961e38, 3.4e38]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(oracle.encode(x, "bf16"), want)
+    want16 = x.astype(np.float16).view(np.uint16)
+    assert np.array_equal(oracle.encode(x, "f16"), want16)
+    # decoders agree with the library casts on every code
+    codes = np.arange(65536, dtype=np.uint16)
+    tb = oracle.decode_table("bf16"); th = oracle.decode_table("f16")
+    lb = torch.from_numpy(codes.view(np.int16)).view(torch.bfloat16).double().numpy()
+    lh = codes.view(np.float16).astype(np.float64)
+    assert np.array_equal(np.isnan(tb), np.isnan(lb)) and np.array_equal(tb[~np.isnan(tb)], lb[~np.isnan(lb)])
+    assert np.array_equal(np.isnan(th), np.isnan(lh)) and np.array_equal(th[~np.isnan(th)], lh[~np.isnan(lh)])
+
+
+def test_quantize_e4m3_rows_rules():
+    g = np.random.default_rng(4)
+    X = g.standard_normal((64, 40)).astype(np.float32)
+    X[3] = 0.0
+    codes, scales = oracle.quantize_e4m3_rows(X)
+    amax = np.abs(X).max(1)
+    assert scales[3] == 1.0 and np.all(codes[3] == 0)
+    nz = amax > 0
+    assert np.array_equal(scales[nz], (amax[nz] / np.float32(448.0)).astype(np.float32))
+    # the largest-magnitude element of each row maps to +-448
+    arg = np.abs(X).argmax(1)
+    top = codes[np.arange(64), arg]
+    assert np.all((top[nz] & 0x7F) == 126)
+    # dequantised values are within half an E4M3 step (relative 2^-4) of x
+    deq = oracle.dequantize(codes, "e4m3", scales)
+    big = np.abs(X) > scales[:, None] * 2.0 ** -6
+    rel = np.abs(deq - X)[big] / np.abs(X)[big]
+    assert rel.max() <= 2.0 ** -4 + 1e-7
+    # same as encoding x / scale element by element
+    q = (X / scales[:, None]).astype(np.float32)
+    assert np.array_equal(codes, oracle.encode(q, "e4m3"))
+
+
+def test_low_precision_operands_use_dequantised_values():
+    M, N, K = 12, 15, 16
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=8)
+    qa, sa = oracle.quantize_e4m3_rows(A); qb, sb = oracle.quantize_e4m3_rows(B)
+    got = oracle.sddmm(rp, ci, qa, qb, vals, a_scale=sa, b_scale=sb)
+    want = oracle.sddmm(rp, ci, oracle.dequantize(qa, "e4m3", sa), oracle.dequantize(qb, "e4m3", sb), vals)
+    np.testing.assert_allclose(got, want, rtol=1e-14)
+    hb = oracle.encode(B, "bf16")
+    np.testing.assert_allclose(oracle.spmm(rp, ci, hb, vals, fmt_b="bf16"),
+                               oracle.spmm(rp, ci, oracle.dequantize(hb, "bf16"), vals), rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# Transpose and merge path
+# ----------------------------------------------------------------------------
+
+def test_transpose_against_scipy_and_involution():
+    sp = pytest.importorskip("scipy.sparse")
+    M, N = 60, 45
+    rp, ci, vals, _, _ = random_case(M, N, 1, 0.1, seed=9)
+    colptr, rowidx, perm = oracle.transpose(rp, ci, N)
+    S = sp.csr_matrix((np.arange(ci.size, dtype=np.int64), ci, rp), shape=(M, N))
+    T = S.tocsc()
+    assert np.array_equal(colptr, T.indptr) and np.array_equal(rowidx, T.indices)
+    assert np.array_equal(perm, T.data)
+    # rows inside a column ascend (stability), and transposing twice gives S back
+    for j in range(N):
+        assert np.all(np.diff(rowidx[colptr[j]:colptr[j + 1]]) > 0)
+    rp2, ci2, perm2 = oracle.transpose(colptr, rowidx, M)
+    assert np.array_equal(rp2, rp) and np.array_equal(ci2, ci)
+    assert np.array_equal(perm[perm2], np.arange(ci.size))
+
+
+def test_merge_path_against_materialised_merge():
+    for seed in range(4):
+        g = np.random.default_rng(seed)
+        M = 40
+        deg = g.integers(0, 6, M); deg[g.integers(0, M, 5)] = 0
+        rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+        nnz = int(rp[-1])
+        # materialise the merge: row-end r has key rowptr[r+1] and sorts before
+        # the nonzero with the same index (type 0 before type 1)
+        items = sorted([(int(rp[r + 1]), 0) for r in range(M)] + [(e, 1) for e in range(nnz)])
+        for d in range(M + nnz + 1):
+            r = sum(1 for it in items[:d] if it[1] == 0)
+            assert oracle.merge_path(rp, d) == (r, d - r)
+
+
+# ----------------------------------------------------------------------------
+# Gradients: closed forms against central finite differences (FP64)
+# ----------------------------------------------------------------------------
+
+def _fd(f, x, v, h=1e-6):
+    return (f(x + h * v) - f(x - h * v)) / (2 * h)
+
+
+def test_sddmm_and_spmm_gradients_fd():
+    M, N, K = 25, 30, 8
+    rp, ci, vals, A, B = random_case(M, N, K, 0.2, seed=12)
+    A = A.astype(np.float64); B = B.astype(np.float64); vals = vals.astype(np.float64)
+    g = np.random.default_rng(13)
+    G = g.standard_normal(ci.size)
+    dA, dB, ds = oracle.sddmm_grads(rp, ci, A, B, vals, G)
+    L = lambda A_, B_, s_: (G * oracle.sddmm(rp, ci, A_, B_, s_)).sum()
+    for _ in range(3):
+        VA, VB, Vs = g.standard_normal(A.shape), g.standard_normal(B.shape), g.standard_normal(vals.shape)
+        assert abs(_fd(lambda t: L(t, B, vals), A, VA) - (dA * VA).sum()) < 1e-6
+        assert abs(_fd(lambda t: L(A, t, vals), B, VB) - (dB * VB).sum()) < 1e-6
+        assert abs(_fd(lambda t: L(A, B, t), vals, Vs) - (ds * Vs).sum()) < 1e-6
+    dY = g.standard_normal((M, K))
+    dB2, ds2 = oracle.spmm_grads(rp, ci, B, vals, dY)
+    L2 = lambda B_, s_: (dY * oracle.spmm(rp, ci, B_, s_)).sum()
+    VB, Vs = g.standard_normal(B.shape), g.standard_normal(vals.shape)
+    assert abs(_fd(lambda t: L2(t, vals), B, VB) - (dB2 * VB).sum()) < 1e-6
+    assert abs(_fd(lambda t: L2(B, t), vals, Vs) - (ds2 * Vs).sum()) < 1e-6
+
+
+def test_gnn_gradient_fd_scale12():
+    """The differentiation workload's check: R-MAT scale 12 copy, K = 8."""
+    P = synth.small_rmat(scale=12, edge_factor=8, K=8, seed=0)
+    H = P.A.astype(np.float64)
+    g = np.random.default_rng(1)
+    dY = g.standard_normal(H.shape)
+    dH = oracle.gnn_grad(P.rowptr, P.colidx, H, dY)
+    L = lambda H_: (dY * oracle.gnn_forward(P.rowptr, P.colidx, H_)[1]).sum()
+    for _ in range(3):
+        V = g.standard_normal(H.shape)
+        fd = _fd(L, H, V)
+        an = (dH * V).sum()
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+    # a few single coordinates, including one in the heaviest row
+    heavy = int(np.argmax(np.diff(P.rowptr)))
+    for (i, k) in [(heavy, 0), (0, 3), (P.M - 1, 7)]:
+        V = np.zeros_like(H); V[i, k] = 1.0
+        assert abs(_fd(L, H, V) - dH[i, k]) <= 1e-6 * max(1.0, abs(dH[i, k]))
