@@ -1,0 +1,214 @@
+/*
+ * spk — local SDDMM / SpMM kernels for NVIDIA GB300 (sm_103a), C ABI.
+ *
+ * The library implements the per-processor Compute phase of a 3D sparse
+ * kernel (SpComm3D, arXiv 2404.19638, Sec. 6.1): the local computation that
+ * runs on local data once communication has delivered it.  With S an M x N
+ * sparse matrix and A (M x K), B (N x K) dense tall-and-skinny factors
+ * (Sec. 3.1):
+ *
+ *   SDDMM   out_e = s_e * <A[i,:], B[j,:]>  for every stored e = (i, j)   (Sec. 3.2, Eq. 1)
+ *   SpMM    C[i,:] = sum_{e=(i,j)} s_e * B[j,:]                          (Sec. 3.2, Eq. 2;
+ *           the text's "S B^T" is read as S B, matching the row-by-row equation)
+ *   SpMM^T  X[j,:] = sum_{e=(i,j)} s_e * Y[i,:]   — the adjoint of SpMM; with
+ *           SDDMM it forms the pair of Sec. 3.2 in which every nonzero takes
+ *           or outputs two dense vectors.
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is a DEVICE pointer owned by the caller; the library
+ *    never allocates device memory.  Schedules, transpose plans and the SpMM
+ *    carry workspace live in caller-provided buffers whose sizes are queried
+ *    first.  Handles own only small host-side metadata.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute calls
+ *    are asynchronous; the *_build calls synchronise `stream` once at the end
+ *    to read back a size.
+ *  - Sparse patterns are CSR with int32 row pointers (M+1) and column indices
+ *    (nnz); nnz < 2^31.  Columns need not be sorted; duplicates are
+ *    independent entries.  Values are passed per call (the pattern stays fixed
+ *    while values change, Sec. 5.1), as FP32 `vals` (NULL = all ones) times an
+ *    optional second FP32 factor `vals2` (NULL = ones), indexed like colidx.
+ *  - Dense matrices are row-major with a leading dimension (elements) >= K.
+ *  - Arithmetic: inputs are widened to FP32 and accumulated in FP32 (no FP64
+ *    on the GPU).  E4M3 operands carry one FP32 scale per row: the value of an
+ *    element is code * scale[row].
+ *  - Errors are returned as spk_status; no exception crosses the ABI.
+ *    spk_last_error() gives a message for the calling thread.  Argument errors
+ *    are detected on the host before any CUDA call.
+ */
+#ifndef SPK_H
+#define SPK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spk_status {
+    SPK_OK = 0,
+    SPK_ERR_ARG = 1,          /* null pointer, negative size, bad flag            */
+    SPK_ERR_SHAPE = 2,        /* leading dimension < K, K < 1, size mismatch      */
+    SPK_ERR_INDEX = 3,        /* malformed CSR found by spk_csr_validate          */
+    SPK_ERR_DTYPE = 4,        /* unsupported dtype or dtype combination           */
+    SPK_ERR_WORKSPACE = 5,    /* caller buffer too small or misaligned            */
+    SPK_ERR_CUDA = 6,         /* a CUDA runtime call or kernel launch failed      */
+    SPK_ERR_TIMEOUT = 7,      /* reserved: no entry point waits on the device     */
+    SPK_ERR_UNSUPPORTED = 8,  /* sizes beyond int32 indexing or the kernel tables */
+    SPK_ERR_STATE = 9         /* handle used before a required build step        */
+} spk_status;
+
+typedef enum spk_dtype {
+    SPK_F32 = 0,              /* IEEE binary32                                     */
+    SPK_BF16 = 1,             /* bfloat16                                          */
+    SPK_F16 = 2,              /* IEEE binary16                                     */
+    SPK_E4M3 = 3              /* OCP FP8 E4M3 with one FP32 scale per row          */
+} spk_dtype;
+
+/* Kernel choice.  Zero fields mean "library default".  See spk_tune_default. */
+typedef struct spk_tune {
+    int32_t variant;        /* 0 default, 1 row-split (one lane group per row),
+                               2 balanced chunks (merge-path schedule, needs spk_schedule_build) */
+    int32_t group_lanes;    /* lanes that share one row of the dense factor: 4, 8, 16, 32 */
+    int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
+    int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
+    int32_t cta_threads;    /* threads per CTA: 128, 256, 512                      */
+} spk_tune;
+
+typedef struct spk_csr_s* spk_csr;       /* pattern of S (+ its schedule)      */
+typedef struct spk_tplan_s* spk_tplan;   /* transpose plan of a pattern        */
+typedef struct spk_batch_s* spk_batch;   /* batched persistent launch          */
+
+/* ---------------------------------------------------------------- misc -- */
+const char* spk_status_string(spk_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* spk_last_error(void);
+int32_t spk_version(void);
+/* The tune a default call would use for this op (0 SDDMM, 1 SpMM, 2 SpMM^T),
+ * dtype of the gathered operand, and K.  Fills *out. */
+spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int32_t K, spk_tune* out);
+
+/* ------------------------------------------------------------- pattern -- */
+/* Wrap a CSR pattern (Sec. 3.1: S is M x N).  rowptr[M+1], colidx[nnz] are
+ * borrowed device pointers that must outlive the handle.  No device work. */
+spk_status spk_csr_create(spk_csr* out, int64_t M, int64_t N, int64_t nnz,
+                          const int32_t* rowptr, const int32_t* colidx);
+spk_status spk_csr_destroy(spk_csr S);
+
+/* Check the pattern on the device: rowptr[0] == 0, rowptr[M] == nnz,
+ * rowptr non-decreasing, 0 <= colidx < N.  d_report is a device int32[4]
+ * the kernel fills: {first error code (0 = valid), first bad index, number of
+ * bad entries, 1 if some row has unsorted or repeated columns}.  The caller
+ * reads it after synchronising `stream`.  Returns SPK_OK if the check was
+ * launched; the verdict is in d_report. */
+spk_status spk_csr_validate(spk_csr S, int32_t* d_report, void* stream);
+
+/* ------------------------------------------------------------ schedule -- */
+/* The balanced schedule cuts the merged sequence of (row ends, nonzeros) into
+ * chunks of about `chunk_work` items (merge-path partition), snapping each cut
+ * back to a row start unless the row holds more than chunk_work nonzeros; such
+ * long rows are split and their partial SpMM sums combined in a fixed order.
+ * It also stores the row index of every nonzero (COO view).  It depends only
+ * on the pattern (Sec. 5.1: built once, reused while values change).
+ * chunk_work: 32 .. 2^20 (0 = default 512). */
+spk_status spk_schedule_size(spk_csr S, int32_t chunk_work, size_t* bytes);
+/* Builds into `storage` (>= spk_schedule_size bytes, 256-byte aligned) and
+ * attaches it to S.  Synchronises `stream` once. */
+spk_status spk_schedule_build(spk_csr S, int32_t chunk_work, void* storage, size_t bytes, void* stream);
+/* nchunks, number of split-row pieces, and chunk_work of the attached schedule. */
+spk_status spk_schedule_info(spk_csr S, int64_t* nchunks, int64_t* npieces, int32_t* chunk_work);
+/* Copy of the schedule's chunk boundaries as (row, nonzero) int32 pairs,
+ * nchunks + 1 of them, into a device buffer (for tests). */
+spk_status spk_schedule_bounds(spk_csr S, int32_t* d_out, void* stream);
+
+/* Bytes of workspace a SpMM on S with K columns needs (carry rows of split
+ * rows under the balanced schedule; 0 for row-split). */
+spk_status spk_spmm_workspace_size(spk_csr S, int32_t K, size_t* bytes);
+
+/* ------------------------------------------------------------- compute -- */
+/* SDDMM, Eq. 1.  A: M x K (dtype dta, leading dim lda, scales a_scale[M] for
+ * E4M3), B: N x K (dtb, ldb, b_scale[N]).  out[nnz] FP32 in colidx order.
+ * Supported (dta, dtb): equal dtypes, or dta = F32 with dtb = BF16 / F16. */
+spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2,
+                     spk_dtype dta, const void* A, int64_t lda, const float* a_scale,
+                     spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale,
+                     int32_t K, float* out, const spk_tune* tune, void* stream);
+
+/* SpMM, Eq. 2.  C (M x K, dtype dtc in {F32, BF16, F16}, leading dim ldc)
+ * = S B, or C += S B with accumulate = 1.  Empty rows are written as zero
+ * (left unchanged when accumulating).  workspace: >= spk_spmm_workspace_size
+ * bytes when the balanced schedule is used (may be NULL otherwise).
+ * Split rows are summed in chunk order: results are deterministic.  Calls that
+ * share one schedule must not overlap on the device. */
+spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
+                    spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
+                    spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate,
+                    void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
+
+/* ----------------------------------------------------- transpose plan -- */
+/* The CSC of S by a stable device radix sort on the column index: colptr[N+1],
+ * rowidx[nnz] (rows ascending inside a column) and perm[nnz] (CSR slot of each
+ * CSC slot), plus a balanced schedule of S^T.  storage holds the plan for its
+ * lifetime; temp is scratch for the build only. */
+spk_status spk_tplan_size(spk_csr S, int32_t chunk_work, size_t* storage_bytes, size_t* temp_bytes);
+spk_status spk_tplan_build(spk_csr S, int32_t chunk_work, void* storage, size_t storage_bytes,
+                           void* temp, size_t temp_bytes, spk_tplan* out, void* stream);
+spk_status spk_tplan_arrays(spk_tplan P, const int32_t** colptr, const int32_t** rowidx,
+                            const int32_t** perm);
+spk_status spk_tplan_destroy(spk_tplan P);
+spk_status spk_spmm_t_workspace_size(spk_tplan P, int32_t K, size_t* bytes);
+
+/* X (N x K) = S^T Y (Y: M x K), or += with accumulate = 1.  vals / vals2 are
+ * indexed like S's colidx (CSR order) and gathered through perm. */
+spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* vals2,
+                      spk_dtype dty, const void* Y, int64_t ldy, const float* y_scale, int32_t K,
+                      spk_dtype dtx, void* X, int64_t ldx, int32_t accumulate,
+                      void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
+
+/* ----------------------------------------------------------- precision -- */
+/* Round-to-nearest-even casts of n FP32 values to BF16 or F16. */
+spk_status spk_cast(const float* x, int64_t n, spk_dtype dt, void* out, void* stream);
+/* Per-row E4M3 quantisation: scale[i] = max_k |X[i,k]| / 448 (1 for an
+ * all-zero row), Q[i,k] = E4M3(X[i,k] / scale[i]) with round-to-nearest-even
+ * and saturation to +-448; the division is IEEE binary32. */
+spk_status spk_quantize_e4m3_rows(const float* X, int64_t M, int64_t K, int64_t ldx,
+                                  uint8_t* Q, int64_t ldq, float* scales, void* stream);
+
+/* ------------------------------------------------------------- batched -- */
+/* Many independent problems in one persistent launch.  Every item names a
+ * pattern (with a balanced schedule attached), its values, dense operands and
+ * output; op is 0 (SDDMM: out = FP32 nnz array) or 1 (SpMM: out = C, FP32).
+ * Items may differ in size, K (1..512) and dtype (F32 or BF16, both operands
+ * alike).  The run is a single kernel launch that pulls (item, chunk) work off
+ * a device counter, so it can be captured in a CUDA graph and replayed; the
+ * counter resets itself at the end of each run.  Pointers are fixed at
+ * creation: replays read whatever the buffers hold at that time. */
+typedef struct spk_batch_item {
+    int32_t op;               /* 0 SDDMM, 1 SpMM                              */
+    spk_csr S;
+    const float* vals;        /* NULL = ones                                  */
+    spk_dtype dt;             /* F32 or BF16                                  */
+    const void* A;            /* SDDMM only: M x K, leading dim lda           */
+    int64_t lda;
+    const void* B;            /* N x K, leading dim ldb                       */
+    int64_t ldb;
+    int32_t K;
+    void* out;                /* SDDMM: float[nnz]; SpMM: float C[M x ldc]    */
+    int64_t ldc;
+    const spk_tune* tune;     /* NULL = default; group_lanes/vecs/unroll used */
+} spk_batch_item;
+
+/* storage: device buffer (256-byte aligned) for descriptors, work counters and
+ * SpMM carry rows; size from spk_batch_size. */
+spk_status spk_batch_size(const spk_batch_item* items, int32_t count, size_t* bytes);
+spk_status spk_batch_create(const spk_batch_item* items, int32_t count, void* storage,
+                            size_t bytes, spk_batch* out, void* stream);
+spk_status spk_batch_run(spk_batch Bt, void* stream);
+/* Number of (item, chunk) work units and CTAs of one run. */
+spk_status spk_batch_info(spk_batch Bt, int64_t* work_units, int32_t* ctas);
+spk_status spk_batch_destroy(spk_batch Bt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPK_H */

@@ -1,0 +1,19 @@
+"""GB300-native local SDDMM / SpMM (the Compute phase of SpComm3D, Sec. 6.1).
+
+    S = CSR(rowptr, colidx, (M, N), vals)        # pattern + balanced schedule
+    out = sddmm(S, A, B)                          # Eq. 1, FP32 per nonzero
+    C = spmm(S, B)                                # Eq. 2
+    X = spmm_t(S, Y)                              # S^T Y via the transpose plan
+
+All arithmetic runs in libspk's CUDA kernels for sm_103a (include/spk.h);
+PyTorch supplies device memory and streams.  There is no CPU fallback: the
+first call raises if libspk.so was not built.
+"""
+from .binding import SpkError, Tune, library_path
+from .sparse import CSR, TransposePlan, DEFAULT_CHUNK_WORK
+from .ops import sddmm, spmm, spmm_t, cast, quantize_e4m3_rows
+from . import autograd
+from .batch import Batch, Item, OP_SDDMM, OP_SPMM
+
+__all__ = ["CSR", "TransposePlan", "sddmm", "spmm", "spmm_t", "cast", "quantize_e4m3_rows", "autograd",
+           "Batch", "Item", "OP_SDDMM", "OP_SPMM", "SpkError", "Tune", "library_path", "DEFAULT_CHUNK_WORK"]

@@ -1,0 +1,484 @@
+// Host side of the C ABI declared in include/spk.h: argument checks (all
+// before any CUDA call), handles, kernel-shape selection and dispatch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+namespace spk {
+
+cudaError_t launch_merge_path_bounds(const int32_t* rowptr, int64_t M, int64_t nnz, int32_t W, int64_t n,
+                                     int2* out, cudaStream_t s);
+
+static const Shape kShapes[kNumShapes] = {
+#define X(i, G_, NV_, U_) {G_, NV_, U_},
+    SPK_SHAPES(X)
+#undef X
+};
+
+int shape_index(int G, int NV, int U)
+{
+    for (int i = 0; i < kNumShapes; ++i)
+        if (kShapes[i].G == G && kShapes[i].NV == NV && kShapes[i].U == U) return i;
+    return -1;
+}
+
+Shape shape_at(int i) { return kShapes[i]; }
+
+cudaError_t launch_sddmm(int dta, int dtb, const Launch& L, const SddmmArgs& a, cudaStream_t s)
+{
+    switch (dtb) {
+    case DT_F32: return launch_sddmm_f32(dta, L, a, s);
+    case DT_BF16: return launch_sddmm_bf16(dta, L, a, s);
+    case DT_F16: return launch_sddmm_f16(dta, L, a, s);
+    case DT_E4M3: return launch_sddmm_e4m3(dta, L, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_spmm(int dtb, const Launch& L, const SpmmArgs& a, cudaStream_t s)
+{
+    switch (dtb) {
+    case DT_F32: return launch_spmm_f32(L, a, s);
+    case DT_BF16: return launch_spmm_bf16(L, a, s);
+    case DT_F16: return launch_spmm_f16(L, a, s);
+    case DT_E4M3: return launch_spmm_e4m3(L, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace spk
+
+using namespace spk;
+
+// ----------------------------------------------------------------------------
+// Errors
+// ----------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static spk_status fail(spk_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+static spk_status cuda_fail(cudaError_t e, const char* where)
+{
+    return fail(SPK_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define REQUIRE(cond, status, ...) \
+    do {                           \
+        if (!(cond)) return fail(status, __VA_ARGS__); \
+    } while (0)
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+static bool valid_dt(int dt) { return dt >= SPK_F32 && dt <= SPK_E4M3; }
+
+extern "C" const char* spk_status_string(spk_status s)
+{
+    switch (s) {
+    case SPK_OK: return "ok";
+    case SPK_ERR_ARG: return "invalid argument";
+    case SPK_ERR_SHAPE: return "invalid shape";
+    case SPK_ERR_INDEX: return "malformed sparse pattern";
+    case SPK_ERR_DTYPE: return "unsupported dtype";
+    case SPK_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case SPK_ERR_CUDA: return "CUDA error";
+    case SPK_ERR_TIMEOUT: return "device wait timed out";
+    case SPK_ERR_UNSUPPORTED: return "unsupported size";
+    case SPK_ERR_STATE: return "handle not ready";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* spk_last_error(void) { return g_err.c_str(); }
+// Not in the public header: lets other translation units set the message.
+extern "C" void spk_internal_set_error(const char* msg) { g_err = msg ? msg : ""; }
+extern "C" int32_t spk_version(void) { return 10000; }
+
+// ----------------------------------------------------------------------------
+// Pattern handles
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_csr_create(spk_csr* out, int64_t M, int64_t N, int64_t nnz, const int32_t* rowptr,
+                                     const int32_t* colidx)
+{
+    REQUIRE(out, SPK_ERR_ARG, "spk_csr_create: out is NULL");
+    *out = nullptr;
+    REQUIRE(M >= 0 && N >= 0 && nnz >= 0, SPK_ERR_ARG, "spk_csr_create: negative size (M=%lld N=%lld nnz=%lld)",
+            (long long)M, (long long)N, (long long)nnz);
+    REQUIRE(M < INT32_MAX && N < INT32_MAX && nnz < INT32_MAX, SPK_ERR_UNSUPPORTED,
+            "spk_csr_create: sizes must be below 2^31-1 (int32 indices)");
+    REQUIRE(rowptr, SPK_ERR_ARG, "spk_csr_create: rowptr is NULL");
+    REQUIRE(colidx || nnz == 0, SPK_ERR_ARG, "spk_csr_create: colidx is NULL");
+    REQUIRE(nnz == 0 || N > 0, SPK_ERR_SHAPE, "spk_csr_create: nonzeros in a matrix with no columns");
+    spk_csr_s* S = new (std::nothrow) spk_csr_s();
+    REQUIRE(S, SPK_ERR_ARG, "spk_csr_create: out of host memory");
+    S->M = M; S->N = N; S->nnz = nnz;
+    S->rowptr = rowptr; S->colidx = colidx;
+    *out = S;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_csr_destroy(spk_csr S)
+{
+    delete S;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_csr_validate(spk_csr S, int32_t* d_report, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_csr_validate: S is NULL");
+    REQUIRE(d_report, SPK_ERR_ARG, "spk_csr_validate: report is NULL");
+    cudaError_t e = launch_validate(S->rowptr, S->colidx, S->M, S->N, S->nnz, d_report, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_csr_validate");
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Schedule
+// ----------------------------------------------------------------------------
+static int32_t chunk_work_or_default(int32_t W) { return W == 0 ? 512 : W; }
+
+extern "C" spk_status spk_schedule_size(spk_csr S, int32_t chunk_work, size_t* bytes)
+{
+    REQUIRE(S && bytes, SPK_ERR_ARG, "spk_schedule_size: NULL argument");
+    const int32_t W = chunk_work_or_default(chunk_work);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_schedule_size: chunk_work %d outside [32, 2^20]", W);
+    *bytes = sched_layout(S->M, S->nnz, W).total;
+    return SPK_OK;
+}
+
+static spk_status attach_schedule(spk_csr_s* S, int32_t W, void* storage, size_t bytes, cudaStream_t s)
+{
+    const SchedLayout L = sched_layout(S->M, S->nnz, W);
+    REQUIRE(storage, SPK_ERR_WORKSPACE, "schedule storage is NULL");
+    REQUIRE(bytes >= L.total, SPK_ERR_WORKSPACE, "schedule storage has %zu bytes, needs %zu", bytes, L.total);
+    REQUIRE((reinterpret_cast<uintptr_t>(storage) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "schedule storage must be 256-byte aligned");
+    char* st = reinterpret_cast<char*>(storage);
+    int64_t np = 0;
+    S->has_sched = false;
+    cudaError_t e = build_schedule(S->rowptr, S->M, S->nnz, W, st, L, &np, s);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule build");
+    S->has_sched = true;
+    S->W = W;
+    S->nchunks = L.nchunks;
+    S->npieces = np;
+    S->rowidx = reinterpret_cast<const int32_t*>(st + L.rowidx);
+    S->bnd = reinterpret_cast<const int2*>(st + L.bnd);
+    S->meta = reinterpret_cast<const int4*>(st + L.meta);
+    S->head_s0 = reinterpret_cast<const int32_t*>(st + L.head_s0);
+    S->slot_np = reinterpret_cast<const int32_t*>(st + L.slot_np);
+    S->cnt = reinterpret_cast<int32_t*>(st + L.cnt);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_schedule_build(spk_csr S, int32_t chunk_work, void* storage, size_t bytes, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_schedule_build: S is NULL");
+    const int32_t W = chunk_work_or_default(chunk_work);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_schedule_build: chunk_work %d outside [32, 2^20]", W);
+    return attach_schedule(S, W, storage, bytes, (cudaStream_t)stream);
+}
+
+extern "C" spk_status spk_schedule_info(spk_csr S, int64_t* nchunks, int64_t* npieces, int32_t* chunk_work)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_schedule_info: S is NULL");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_schedule_info: no schedule attached");
+    if (nchunks) *nchunks = S->nchunks;
+    if (npieces) *npieces = S->npieces;
+    if (chunk_work) *chunk_work = S->W;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_schedule_bounds(spk_csr S, int32_t* d_out, void* stream)
+{
+    REQUIRE(S && d_out, SPK_ERR_ARG, "spk_schedule_bounds: NULL argument");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_schedule_bounds: no schedule attached");
+    cudaError_t e = cudaMemcpyAsync(d_out, S->bnd, (size_t)(S->nchunks + 1) * 8, cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_schedule_bounds");
+    return SPK_OK;
+}
+
+// Raw merge-path split points (row, nonzero) at diagonals 0, W, 2W, ... (n+1
+// of them): not part of the public header; used by tests to check the search.
+extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int32_t* d_out, void* stream)
+{
+    REQUIRE(S && d_out && W > 0 && n >= 0, SPK_ERR_ARG, "spk_merge_path_points: bad argument");
+    cudaError_t e = launch_merge_path_bounds(S->rowptr, S->M, S->nnz, W, n, reinterpret_cast<int2*>(d_out),
+                                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_merge_path_points");
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Kernel shape selection
+// ----------------------------------------------------------------------------
+enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
+
+static void default_shape(int op, int nvec, int* G, int* NV, int* U)
+{
+    if (nvec <= 4) { *G = 4; *NV = 1; *U = 4; }
+    else if (nvec <= 8) { *G = 8; *NV = 1; *U = 8; }
+    else if (nvec <= 16) { *G = 16; *NV = 1; *U = (op == OP_SDDMM) ? 4 : 8; }
+    else if (nvec <= 32) { *G = 32; *NV = 1; *U = 8; }
+    else if (nvec <= 64) { *G = 32; *NV = 2; *U = 4; }
+    else { *G = 32; *NV = 4; *U = 4; }
+}
+
+static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, const spk_tune* t, Launch* L)
+{
+    const int variant = (t && t->variant) ? t->variant : (S->has_sched ? 2 : 1);
+    REQUIRE(variant == 1 || variant == 2, SPK_ERR_ARG, "tune.variant %d is not 0, 1 or 2", variant);
+    REQUIRE(variant == 1 || S->has_sched, SPK_ERR_STATE, "balanced variant needs spk_schedule_build first");
+    const int vecn = vec ? vec_elems(dtb) : 1;
+    const int nvec = K / vecn;
+    int G, NV, U;
+    default_shape(op, nvec, &G, &NV, &U);
+    if (t && t->group_lanes) G = t->group_lanes;
+    if (t && t->vecs_per_lane) NV = t->vecs_per_lane;
+    if (t && t->unroll) U = t->unroll;
+    const int idx = shape_index(G, NV, U);
+    REQUIRE(idx >= 0, SPK_ERR_UNSUPPORTED, "no kernel compiled for group_lanes=%d vecs_per_lane=%d unroll=%d",
+            G, NV, U);
+    const int threads = (t && t->cta_threads) ? t->cta_threads : 256;
+    REQUIRE(threads == 128 || threads == 256, SPK_ERR_ARG, "tune.cta_threads must be 128 or 256");
+    L->shape = idx;
+    L->vec = vec;
+    L->threads = threads;
+    L->chunks = (variant == 2);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int32_t K, spk_tune* out)
+{
+    REQUIRE(S && out, SPK_ERR_ARG, "spk_tune_default: NULL argument");
+    REQUIRE(op >= 0 && op <= 2 && valid_dt(dt) && K >= 1, SPK_ERR_ARG, "spk_tune_default: bad op/dtype/K");
+    const bool vec = (K % vec_elems(dt)) == 0;
+    Launch L;
+    const spk_csr_s* P = S;
+    spk_status st = resolve(P, op, dt, K, vec, nullptr, &L);
+    if (st != SPK_OK) return st;
+    const Shape sh = shape_at(L.shape);
+    out->variant = L.chunks ? 2 : 1;
+    out->group_lanes = sh.G;
+    out->vecs_per_lane = sh.NV;
+    out->unroll = sh.U;
+    out->cta_threads = L.threads;
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// SDDMM
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2, spk_dtype dta, const void* A,
+                                int64_t lda, const float* a_scale, spk_dtype dtb, const void* B, int64_t ldb,
+                                const float* b_scale, int32_t K, float* out, const spk_tune* tune, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_sddmm: S is NULL");
+    REQUIRE(valid_dt(dta) && valid_dt(dtb), SPK_ERR_DTYPE, "spk_sddmm: unknown dtype");
+    REQUIRE(dta == dtb || (dta == SPK_F32 && (dtb == SPK_BF16 || dtb == SPK_F16)), SPK_ERR_DTYPE,
+            "spk_sddmm: dtype pair (%d, %d) not supported", (int)dta, (int)dtb);
+    REQUIRE(K >= 1, SPK_ERR_SHAPE, "spk_sddmm: K must be >= 1 (got %d)", K);
+    REQUIRE(lda >= K && ldb >= K, SPK_ERR_SHAPE, "spk_sddmm: leading dimensions must be >= K");
+    REQUIRE(S->nnz == 0 || (A && B && out), SPK_ERR_ARG, "spk_sddmm: NULL operand");
+    REQUIRE(dta != SPK_E4M3 || (a_scale && b_scale), SPK_ERR_ARG, "spk_sddmm: E4M3 needs a_scale and b_scale");
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_sddmm: pattern belongs to a transpose plan");
+    if (S->nnz == 0) return SPK_OK;
+    const int vecn = vec_elems(dtb);
+    const bool vec = (K % vecn) == 0 && aligned16(A) && aligned16(B) && (lda * dt_bytes(dta)) % 16 == 0 &&
+                     (ldb * dt_bytes(dtb)) % 16 == 0;
+    Launch L;
+    spk_status st = resolve(S, OP_SDDMM, dtb, K, vec, tune, &L);
+    if (st != SPK_OK) return st;
+    SddmmArgs a;
+    a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = K;
+    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
+    a.vals = vals; a.vals2 = vals2;
+    a.A = A; a.lda = lda; a.a_scale = a_scale;
+    a.B = B; a.ldb = ldb; a.b_scale = b_scale;
+    a.out = out;
+    a.bnd = L.chunks ? S->bnd : nullptr;
+    a.nchunks = S->nchunks;
+    cudaError_t e = launch_sddmm(dta, dtb, L, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_sddmm launch");
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
+// SpMM / SpMM^T
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_spmm_workspace_size(spk_csr S, int32_t K, size_t* bytes)
+{
+    REQUIRE(S && bytes && K >= 1, SPK_ERR_ARG, "spk_spmm_workspace_size: bad argument");
+    *bytes = S->has_sched ? (size_t)S->npieces * (size_t)K * 4 : 0;
+    return SPK_OK;
+}
+
+static spk_status spmm_common(const char* name, const spk_csr_s* S, const float* vals, const float* vals2,
+                              spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
+                              spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate, void* ws, size_t ws_bytes,
+                              const spk_tune* tune, cudaStream_t stream)
+{
+    REQUIRE(valid_dt(dtb), SPK_ERR_DTYPE, "%s: unknown input dtype", name);
+    REQUIRE(dtc == SPK_F32 || dtc == SPK_BF16 || dtc == SPK_F16, SPK_ERR_DTYPE,
+            "%s: output dtype must be F32, BF16 or F16", name);
+    REQUIRE(K >= 1, SPK_ERR_SHAPE, "%s: K must be >= 1 (got %d)", name, K);
+    REQUIRE(ldb >= K && ldc >= K, SPK_ERR_SHAPE, "%s: leading dimensions must be >= K", name);
+    REQUIRE(accumulate == 0 || accumulate == 1, SPK_ERR_ARG, "%s: accumulate must be 0 or 1", name);
+    REQUIRE(S->M == 0 || C, SPK_ERR_ARG, "%s: output is NULL", name);
+    REQUIRE(S->nnz == 0 || B, SPK_ERR_ARG, "%s: dense input is NULL", name);
+    REQUIRE(dtb != SPK_E4M3 || b_scale, SPK_ERR_ARG, "%s: E4M3 input needs row scales", name);
+    if (S->M == 0) return SPK_OK;
+    const int vecn = vec_elems(dtb);
+    const bool vec = (K % vecn) == 0 && aligned16(B) && aligned16(C) && (ldb * dt_bytes(dtb)) % 16 == 0 &&
+                     (ldc * dt_bytes(dtc)) % 16 == 0;
+    Launch L;
+    spk_status st = resolve(S, OP_SPMM, dtb, K, vec, tune, &L);
+    if (st != SPK_OK) return st;
+    if (L.chunks && S->npieces > 0) {
+        const size_t need = (size_t)S->npieces * (size_t)K * 4;
+        REQUIRE(ws && ws_bytes >= need, SPK_ERR_WORKSPACE, "%s: workspace has %zu bytes, needs %zu", name,
+                ws ? ws_bytes : (size_t)0, need);
+        REQUIRE(aligned16(ws), SPK_ERR_WORKSPACE, "%s: workspace must be 16-byte aligned", name);
+    }
+    SpmmArgs a;
+    a.M = S->M; a.N = S->N; a.K = K;
+    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vperm = S->vperm;
+    a.vals = vals; a.vals2 = vals2;
+    a.B = B; a.ldb = ldb; a.b_scale = b_scale;
+    a.C = C; a.ldc = ldc; a.dtc = dtc; a.accumulate = accumulate;
+    a.bnd = L.chunks ? S->bnd : nullptr;
+    a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
+    a.carry = reinterpret_cast<float*>(ws);
+    a.nchunks = S->nchunks;
+    cudaError_t e = launch_spmm(dtb, L, a, stream);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2, spk_dtype dtb, const void* B,
+                               int64_t ldb, const float* b_scale, int32_t K, spk_dtype dtc, void* C, int64_t ldc,
+                               int32_t accumulate, void* workspace, size_t ws_bytes, const spk_tune* tune,
+                               void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_spmm: S is NULL");
+    return spmm_common("spk_spmm", S, vals, vals2, dtb, B, ldb, b_scale, K, dtc, C, ldc, accumulate, workspace,
+                       ws_bytes, tune, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Transpose plan
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_tplan_size(spk_csr S, int32_t chunk_work, size_t* storage_bytes, size_t* temp_bytes)
+{
+    REQUIRE(S && storage_bytes && temp_bytes, SPK_ERR_ARG, "spk_tplan_size: NULL argument");
+    const int32_t W = chunk_work_or_default(chunk_work);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_tplan_size: chunk_work %d outside [32, 2^20]", W);
+    const TplanLayout L = tplan_layout(S->M, S->N, S->nnz, W);
+    *storage_bytes = L.total;
+    *temp_bytes = L.temp_total;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tplan_build(spk_csr S, int32_t chunk_work, void* storage, size_t storage_bytes,
+                                      void* temp, size_t temp_bytes, spk_tplan* out, void* stream)
+{
+    REQUIRE(S && out, SPK_ERR_ARG, "spk_tplan_build: NULL argument");
+    *out = nullptr;
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_tplan_build: pattern already belongs to a transpose plan");
+    const int32_t W = chunk_work_or_default(chunk_work);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_tplan_build: chunk_work %d outside [32, 2^20]", W);
+    const TplanLayout L = tplan_layout(S->M, S->N, S->nnz, W);
+    REQUIRE(storage && storage_bytes >= L.total, SPK_ERR_WORKSPACE, "spk_tplan_build: storage needs %zu bytes",
+            L.total);
+    REQUIRE(temp && temp_bytes >= L.temp_total, SPK_ERR_WORKSPACE, "spk_tplan_build: temp needs %zu bytes",
+            L.temp_total);
+    REQUIRE((reinterpret_cast<uintptr_t>(storage) & 255u) == 0 && (reinterpret_cast<uintptr_t>(temp) & 255u) == 0,
+            SPK_ERR_WORKSPACE, "spk_tplan_build: buffers must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* st = reinterpret_cast<char*>(storage);
+    cudaError_t e = build_transpose(S->rowptr, S->colidx, S->M, S->N, S->nnz, st, reinterpret_cast<char*>(temp), L, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_tplan_build");
+    spk_tplan_s* P = new (std::nothrow) spk_tplan_s();
+    REQUIRE(P, SPK_ERR_ARG, "spk_tplan_build: out of host memory");
+    P->M = S->M; P->N = S->N;
+    P->colptr = reinterpret_cast<const int32_t*>(st + L.colptr);
+    P->rowidx = reinterpret_cast<const int32_t*>(st + L.rowidx);
+    P->perm = reinterpret_cast<const int32_t*>(st + L.perm);
+    spk_csr_s& T = P->St;
+    T = spk_csr_s();
+    T.M = S->N; T.N = S->M; T.nnz = S->nnz;
+    T.rowptr = P->colptr; T.colidx = P->rowidx; T.vperm = P->perm;
+    spk_status ss = attach_schedule(&T, W, st + L.sched, L.sl.total, s);
+    if (ss != SPK_OK) { delete P; return ss; }
+    *out = P;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tplan_arrays(spk_tplan P, const int32_t** colptr, const int32_t** rowidx,
+                                       const int32_t** perm)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_tplan_arrays: P is NULL");
+    if (colptr) *colptr = P->colptr;
+    if (rowidx) *rowidx = P->rowidx;
+    if (perm) *perm = P->perm;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tplan_destroy(spk_tplan P)
+{
+    delete P;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_spmm_t_workspace_size(spk_tplan P, int32_t K, size_t* bytes)
+{
+    REQUIRE(P && bytes && K >= 1, SPK_ERR_ARG, "spk_spmm_t_workspace_size: bad argument");
+    *bytes = (size_t)P->St.npieces * (size_t)K * 4;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* vals2, spk_dtype dty, const void* Y,
+                                 int64_t ldy, const float* y_scale, int32_t K, spk_dtype dtx, void* X, int64_t ldx,
+                                 int32_t accumulate, void* workspace, size_t ws_bytes, const spk_tune* tune,
+                                 void* stream)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_spmm_t: P is NULL");
+    return spmm_common("spk_spmm_t", &P->St, vals, vals2, dty, Y, ldy, y_scale, K, dtx, X, ldx, accumulate,
+                       workspace, ws_bytes, tune, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Precision
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_cast(const float* x, int64_t n, spk_dtype dt, void* out, void* stream)
+{
+    REQUIRE(n >= 0, SPK_ERR_ARG, "spk_cast: negative size");
+    REQUIRE(dt == SPK_BF16 || dt == SPK_F16, SPK_ERR_DTYPE, "spk_cast: target must be BF16 or F16");
+    REQUIRE(n == 0 || (x && out), SPK_ERR_ARG, "spk_cast: NULL buffer");
+    cudaError_t e = launch_cast(x, n, dt, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_cast");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_quantize_e4m3_rows(const float* X, int64_t M, int64_t K, int64_t ldx, uint8_t* Q,
+                                             int64_t ldq, float* scales, void* stream)
+{
+    REQUIRE(M >= 0 && K >= 1, SPK_ERR_SHAPE, "spk_quantize_e4m3_rows: bad shape");
+    REQUIRE(ldx >= K && ldq >= K, SPK_ERR_SHAPE, "spk_quantize_e4m3_rows: leading dimensions must be >= K");
+    REQUIRE(M == 0 || (X && Q && scales), SPK_ERR_ARG, "spk_quantize_e4m3_rows: NULL buffer");
+    cudaError_t e = launch_quant_e4m3(X, M, K, ldx, Q, ldq, scales, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_quantize_e4m3_rows");
+    return SPK_OK;
+}

@@ -1,0 +1,323 @@
+// Batched persistent launch: many independent SDDMM / SpMM problems of uneven
+// size in ONE kernel.  Each item is cut into work units (one warp's worth of
+// balanced-schedule chunks, times the K blocks of an SpMM); a persistent grid
+// of one wave of CTAs pulls units off a device counter.  No warp ever waits on
+// another: split SpMM rows are finished by their last-arriving piece (see
+// spmm_impl.cuh), and the last warp to leave resets the counters, so the run
+// can be captured in a CUDA graph and replayed.
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sddmm_impl.cuh"
+#include "spmm_impl.cuh"
+
+namespace spk {
+
+struct BatchDesc {
+    int32_t op;      // 0 SDDMM, 1 SpMM
+    int32_t cls;     // (dtype, shape) class of the device routine
+    int32_t nkb;     // K blocks (SpMM)
+    int32_t gpw;     // lane groups per warp = 32 / G
+    SddmmArgs sd;
+    SpmmArgs sp;
+};
+
+// (G, NV, U) shapes available to batched items; class = dtype * 8 + position
+// in this list.  Each (op, class) routine is a separate non-inlined function,
+// so the merged kernel's register count is the largest routine's (capped at
+// 128 for two resident CTAs per SM); BF16 uses only the U = 4, NV = 1 shapes,
+// which fit that budget without spilling.
+#define SPK_BATCH_SHAPES(X) \
+    X(0, 4, 1, 4)           \
+    X(1, 8, 1, 4)           \
+    X(2, 8, 1, 8)           \
+    X(3, 16, 1, 4)          \
+    X(4, 16, 2, 4)
+
+constexpr int kBatchShapes = 5;
+static const Shape kBatchShapeList[kBatchShapes] = {
+#define X(i, G_, NV_, U_) {G_, NV_, U_},
+    SPK_BATCH_SHAPES(X)
+#undef X
+};
+
+template <int DT, int G, int NV, int U>
+__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit)
+{
+    const Group<G> g;
+    const int64_t c = unit * (32 / G) + ((threadIdx.x & 31) / G);
+    if (c >= a.nchunks) return;
+    const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+    sddmm_span<DT, DT, vec_elems(DT), G, NV, U, false>(a, g, b0.x, b0.y, b1.y);
+}
+
+template <int DT, int G, int NV, int U>
+__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb)
+{
+    const Group<G> g;
+    const int kb = (int)(unit % nkb);
+    const int64_t c = (unit / nkb) * (32 / G) + ((threadIdx.x & 31) / G);
+    if (c >= a.nchunks) return;
+    const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+    const int4 m = a.meta[c];
+    if (b1.y == b0.y && m.z < b0.x) return;
+    const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
+    spmm_span<DT, vec_elems(DT), G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+}
+
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
+                                               const int64_t* __restrict__ unit_begin, int64_t total_units,
+                                               unsigned long long* counter, unsigned int* done)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(counter, 1ull);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if ((int64_t)u >= total_units) break;
+        int lo = 0, hi = count - 1;                  // last item with unit_begin <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(unit_begin + mid) <= (int64_t)u) lo = mid; else hi = mid - 1;
+        }
+        const BatchDesc& d = descs[lo];
+        const int64_t local = (int64_t)u - __ldg(unit_begin + lo);
+        const int cls = d.cls;
+        if (d.op == 0) {
+            switch (cls) {
+#define X(i, G_, NV_, U_)                                                           \
+    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local); break;              \
+    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local); break;
+                SPK_BATCH_SHAPES(X)
+#undef X
+            }
+        } else {
+            switch (cls) {
+#define X(i, G_, NV_, U_)                                                           \
+    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb); break;        \
+    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb); break;
+                SPK_BATCH_SHAPES(X)
+#undef X
+            }
+        }
+        __syncwarp();
+    }
+    // Leave: the last warp of the grid resets the counters for the next run.
+    if (lane == 0) {
+        __threadfence();
+        const unsigned total_warps = gridDim.x * (blockDim.x / 32);
+        const unsigned old = atomicAdd(done, 1u);
+        if (old == total_warps - 1) {
+            atomicExch(counter, 0ull);
+            atomicExch(done, 0u);
+        }
+    }
+}
+
+}  // namespace spk
+
+using namespace spk;
+
+struct spk_batch_s {
+    int32_t count;
+    int64_t total_units;
+    int32_t grid;
+    const BatchDesc* d_descs;
+    const int64_t* d_unit_begin;
+    unsigned long long* d_counter;
+    unsigned int* d_done;
+};
+
+// The library-wide last-error slot lives in api.cu.
+extern "C" void spk_internal_set_error(const char* msg);
+
+static spk_status bfail(spk_status s, const std::string& msg)
+{
+    spk_internal_set_error(msg.c_str());
+    return s;
+}
+
+struct BatchPlan {
+    std::vector<BatchDesc> descs;
+    std::vector<int64_t> unit_begin;
+    size_t off_descs, off_units, off_counter, off_done, off_carry, total;
+    std::vector<size_t> carry_off;   // per item (SpMM), relative to off_carry
+};
+
+static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPlan& P)
+{
+    if (!items || count <= 0) return bfail(SPK_ERR_ARG, "spk_batch: items is NULL or count <= 0");
+    P.descs.assign(count, BatchDesc());
+    P.unit_begin.assign((size_t)count + 1, 0);
+    P.carry_off.assign(count, 0);
+    size_t carry = 0;
+    int64_t units = 0;
+    for (int32_t m = 0; m < count; ++m) {
+        const spk_batch_item& it = items[m];
+        const std::string where = "spk_batch item " + std::to_string(m) + ": ";
+        if (it.op != 0 && it.op != 1) return bfail(SPK_ERR_ARG, where + "op must be 0 (SDDMM) or 1 (SpMM)");
+        if (!it.S) return bfail(SPK_ERR_ARG, where + "S is NULL");
+        const spk_csr_s* S = it.S;
+        if (S->vperm) return bfail(SPK_ERR_ARG, where + "transposed patterns are not batched");
+        if (!S->has_sched) return bfail(SPK_ERR_STATE, where + "pattern needs spk_schedule_build first");
+        if (it.dt != SPK_F32 && it.dt != SPK_BF16) return bfail(SPK_ERR_DTYPE, where + "dtype must be F32 or BF16");
+        if (it.K < 1 || it.K > 128) return bfail(SPK_ERR_SHAPE, where + "K must be in [1, 128]");
+        const int vecn = vec_elems(it.dt);
+        if (it.K % vecn) return bfail(SPK_ERR_UNSUPPORTED, where + "K must be a multiple of 16 bytes of elements");
+        if (it.ldb < it.K || (it.ldb * dt_bytes(it.dt)) % 16 || (reinterpret_cast<uintptr_t>(it.B) & 15))
+            return bfail(SPK_ERR_SHAPE, where + "B must be 16-byte aligned with ldb >= K");
+        if (S->nnz > 0 && !it.B) return bfail(SPK_ERR_ARG, where + "B is NULL");
+        if (!it.out && (it.op == 1 ? S->M > 0 : S->nnz > 0)) return bfail(SPK_ERR_ARG, where + "out is NULL");
+        if (it.op == 0) {
+            if (it.lda < it.K || (it.lda * dt_bytes(it.dt)) % 16 || (reinterpret_cast<uintptr_t>(it.A) & 15))
+                return bfail(SPK_ERR_SHAPE, where + "A must be 16-byte aligned with lda >= K");
+            if (S->nnz > 0 && !it.A) return bfail(SPK_ERR_ARG, where + "A is NULL");
+        } else {
+            if (it.ldc < it.K || (it.ldc * 4) % 16 || (reinterpret_cast<uintptr_t>(it.out) & 15))
+                return bfail(SPK_ERR_SHAPE, where + "C must be 16-byte aligned FP32 with ldc >= K");
+            for (int32_t q = 0; q < m; ++q)
+                if (items[q].op == 1 && items[q].S == it.S)
+                    return bfail(SPK_ERR_ARG, where + "two SpMM items share one pattern handle");
+        }
+        // shape
+        const int nvec = it.K / vecn;
+        // Register budget of the merged kernel (2 CTAs of 256 threads per SM):
+        // BF16 rows (8 values per 16-byte vector) keep 4 nonzeros in flight.
+        const bool bf = (it.dt == SPK_BF16);
+        if (nvec > (bf ? 16 : 32))
+            return bfail(SPK_ERR_UNSUPPORTED, where + "batched K is limited to 128 (F32) / 128 (BF16)");
+        int G, NV, U;
+        if (nvec <= 4) { G = 4; NV = 1; U = 4; }
+        else if (nvec <= 8) { G = 8; NV = 1; U = bf ? 4 : 8; }
+        else if (nvec <= 16) { G = 16; NV = 1; U = 4; }
+        else { G = 16; NV = 2; U = 4; }
+        if (it.tune) {
+            if (it.tune->group_lanes) G = it.tune->group_lanes;
+            if (it.tune->vecs_per_lane) NV = it.tune->vecs_per_lane;
+            if (it.tune->unroll) U = it.tune->unroll;
+        }
+        int sidx = -1;
+        for (int q = 0; q < kBatchShapes; ++q)
+            if (kBatchShapeList[q].G == G && kBatchShapeList[q].NV == NV && kBatchShapeList[q].U == U) sidx = q;
+        if (sidx < 0 || (it.dt == SPK_BF16 && (sidx == 2 || sidx == 4)))
+            return bfail(SPK_ERR_UNSUPPORTED, where + "shape not available in batched mode");
+        BatchDesc& d = P.descs[m];
+        d.op = it.op;
+        d.cls = (it.dt == SPK_BF16 ? 8 : 0) + sidx;
+        d.gpw = 32 / G;
+        d.nkb = 1;
+        const int64_t wunits = (S->nchunks + d.gpw - 1) / d.gpw;
+        if (it.op == 0) {
+            SddmmArgs& a = d.sd;
+            a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = it.K;
+            a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
+            a.vals = it.vals; a.vals2 = nullptr;
+            a.A = it.A; a.lda = it.lda; a.a_scale = nullptr;
+            a.B = it.B; a.ldb = it.ldb; a.b_scale = nullptr;
+            a.out = reinterpret_cast<float*>(it.out);
+            a.bnd = S->bnd; a.nchunks = S->nchunks;
+            P.unit_begin[m + 1] = units + (S->nnz > 0 ? wunits : 0);
+        } else {
+            d.nkb = (nvec + G * NV - 1) / (G * NV);
+            SpmmArgs& a = d.sp;
+            a.M = S->M; a.N = S->N; a.K = it.K;
+            a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vperm = nullptr;
+            a.vals = it.vals; a.vals2 = nullptr;
+            a.B = it.B; a.ldb = it.ldb; a.b_scale = nullptr;
+            a.C = it.out; a.ldc = it.ldc; a.dtc = SPK_F32; a.accumulate = 0;
+            a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
+            a.carry = nullptr;   // set at create time
+            a.nchunks = S->nchunks;
+            P.carry_off[m] = carry;
+            carry += align256((size_t)S->npieces * it.K * 4);
+            P.unit_begin[m + 1] = units + (S->M > 0 ? wunits * d.nkb : 0);
+        }
+        units = P.unit_begin[m + 1];
+    }
+    size_t off = 0;
+    P.off_descs = off;   off += align256(sizeof(BatchDesc) * (size_t)count);
+    P.off_units = off;   off += align256(sizeof(int64_t) * ((size_t)count + 1));
+    P.off_counter = off; off += 256;
+    P.off_done = off;    off += 256;
+    P.off_carry = off;   off += carry;
+    P.total = off;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_batch_size(const spk_batch_item* items, int32_t count, size_t* bytes)
+{
+    if (!bytes) return bfail(SPK_ERR_ARG, "spk_batch_size: bytes is NULL");
+    BatchPlan P;
+    spk_status s = plan_batch(items, count, P);
+    if (s != SPK_OK) return s;
+    *bytes = P.total;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_batch_create(const spk_batch_item* items, int32_t count, void* storage, size_t bytes,
+                                       spk_batch* out, void* stream)
+{
+    if (!out) return bfail(SPK_ERR_ARG, "spk_batch_create: out is NULL");
+    *out = nullptr;
+    BatchPlan P;
+    spk_status s = plan_batch(items, count, P);
+    if (s != SPK_OK) return s;
+    if (!storage || bytes < P.total) return bfail(SPK_ERR_WORKSPACE, "spk_batch_create: storage too small");
+    if (reinterpret_cast<uintptr_t>(storage) & 255u)
+        return bfail(SPK_ERR_WORKSPACE, "spk_batch_create: storage must be 256-byte aligned");
+    char* st = reinterpret_cast<char*>(storage);
+    for (int32_t m = 0; m < count; ++m)
+        if (P.descs[m].op == 1) P.descs[m].sp.carry = reinterpret_cast<float*>(st + P.off_carry + P.carry_off[m]);
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(st + P.off_descs, P.descs.data(), sizeof(BatchDesc) * count,
+                                    cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st + P.off_units, P.unit_begin.data(), sizeof(int64_t) * (count + 1),
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st + P.off_counter, 0, 512, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, 0);
+    if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
+    spk_batch_s* B = new (std::nothrow) spk_batch_s();
+    if (!B) return bfail(SPK_ERR_ARG, "spk_batch_create: out of host memory");
+    B->count = count;
+    B->total_units = P.unit_begin[count];
+    B->grid = sms * (per_sm > 0 ? per_sm : 1);
+    B->d_descs = reinterpret_cast<const BatchDesc*>(st + P.off_descs);
+    B->d_unit_begin = reinterpret_cast<const int64_t*>(st + P.off_units);
+    B->d_counter = reinterpret_cast<unsigned long long*>(st + P.off_counter);
+    B->d_done = reinterpret_cast<unsigned int*>(st + P.off_done);
+    *out = B;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_batch_run(spk_batch B, void* stream)
+{
+    if (!B) return bfail(SPK_ERR_ARG, "spk_batch_run: handle is NULL");
+    if (B->total_units == 0) return SPK_OK;
+    k_batch<<<B->grid, 256, 0, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
+                                                        B->d_counter, B->d_done);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_run: ") + cudaGetErrorString(e));
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_batch_info(spk_batch B, int64_t* work_units, int32_t* ctas)
+{
+    if (!B) return bfail(SPK_ERR_ARG, "spk_batch_info: handle is NULL");
+    if (work_units) *work_units = B->total_units;
+    if (ctas) *ctas = B->grid;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_batch_destroy(spk_batch B)
+{
+    delete B;
+    return SPK_OK;
+}

@@ -1,0 +1,312 @@
+// Internal declarations shared by the CUDA translation units of libspk.
+//
+// Data layout in HBM (all caller-owned):
+//   S      CSR, int32 rowptr[M+1], colidx[nnz]; values FP32 per call
+//   A, B   row-major, leading dimension in elements, one "row" = one dense
+//          vector a_i / b_j of Sec. 3.1
+//   out    SDDMM: FP32 per nonzero, in colidx order; SpMM: C row-major
+// A lane group of G lanes owns one dense row at a time; lane gl holds the
+// 16-byte vectors v = gl + G*t (t < NV) of each K block, so one warp-wide
+// 128-bit load covers whole 128-byte lines of the gathered rows.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "spk.h"
+
+namespace spk {
+
+enum : int { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2, DT_E4M3 = 3 };
+
+__host__ __device__ constexpr int dt_bytes(int dt) { return dt == DT_F32 ? 4 : (dt == DT_E4M3 ? 1 : 2); }
+// Elements in one 16-byte vector of the gathered operand.
+__host__ __device__ constexpr int vec_elems(int dt) { return 16 / dt_bytes(dt); }
+
+// ----------------------------------------------------------------------------
+// Element loads: N consecutive elements of type DT at element index idx,
+// widened to float.  The address must be aligned to min(16, N * bytes).
+// Gathered rows are read through the read-only path (ld.global.nc).
+// ----------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float unpack_one(const uint32_t* w, int k)
+{
+    if constexpr (DT == DT_F32) {
+        return __uint_as_float(w[k]);
+    } else if constexpr (DT == DT_BF16) {
+        uint32_t x = w[k >> 1];
+        return __uint_as_float((k & 1) ? (x & 0xffff0000u) : (x << 16));
+    } else if constexpr (DT == DT_F16) {
+        uint32_t x = w[k >> 1];
+        unsigned short h = (unsigned short)((k & 1) ? (x >> 16) : (x & 0xffffu));
+        return __half2float(__ushort_as_half(h));
+    } else {
+        uint32_t x = w[k >> 2];
+        __nv_fp8_storage_t q = (__nv_fp8_storage_t)((x >> (8 * (k & 3))) & 0xffu);
+        __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
+        return __half2float(__half(hr));
+    }
+}
+
+template <int DT, int N>
+__device__ __forceinline__ void load_elems(const void* base, int64_t idx, float* out)
+{
+    constexpr int TB = N * dt_bytes(DT);
+    constexpr int NW = (TB + 3) / 4;
+    uint32_t w[NW];
+    const char* p = reinterpret_cast<const char*>(base) + idx * dt_bytes(DT);
+    if constexpr (TB >= 16) {
+#pragma unroll
+        for (int q = 0; q < TB / 16; ++q) {
+            uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + q);
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+    } else if constexpr (TB == 8) {
+        uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    } else if constexpr (TB == 4) {
+        w[0] = __ldg(reinterpret_cast<const unsigned int*>(p));
+    } else if constexpr (TB == 2) {
+        w[0] = __ldg(reinterpret_cast<const unsigned short*>(p));
+    } else {
+        w[0] = __ldg(reinterpret_cast<const unsigned char*>(p));
+    }
+    if constexpr (DT == DT_E4M3 && N >= 2) {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) {
+            uint32_t x = w[k >> 2];
+            __nv_fp8x2_storage_t q2 = (__nv_fp8x2_storage_t)((x >> (8 * (k & 3))) & 0xffffu);
+            __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q2, __NV_E4M3);
+            float2 f = __half22float2(__half2(hr));
+            out[k] = f.x; out[k + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) out[k] = unpack_one<DT>(w, k);
+    }
+}
+
+// Plain (coherent, L1-bypassing) load of C for accumulate and of the carry rows.
+template <int DT, int N>
+__device__ __forceinline__ void load_elems_cg(const void* base, int64_t idx, float* out)
+{
+    constexpr int TB = N * dt_bytes(DT);
+    constexpr int NW = (TB + 3) / 4;
+    uint32_t w[NW];
+    const char* p = reinterpret_cast<const char*>(base) + idx * dt_bytes(DT);
+    if constexpr (TB >= 16) {
+#pragma unroll
+        for (int q = 0; q < TB / 16; ++q) {
+            uint4 v = __ldcg(reinterpret_cast<const uint4*>(p) + q);
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+    } else if constexpr (TB == 8) {
+        uint2 v = __ldcg(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    } else if constexpr (TB == 4) {
+        w[0] = __ldcg(reinterpret_cast<const unsigned int*>(p));
+    } else {
+        w[0] = __ldcg(reinterpret_cast<const unsigned short*>(p));
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = unpack_one<DT>(w, k);
+}
+
+// Store N floats as DT (F32, BF16 or F16; round-to-nearest-even), streaming
+// (evict-first) so that output rows do not displace gathered rows in L2.
+template <int DT, int N>
+__device__ __forceinline__ void store_elems(void* base, int64_t idx, const float* v)
+{
+    constexpr int TB = N * dt_bytes(DT);
+    constexpr int NW = (TB + 3) / 4;
+    uint32_t w[NW];
+    if constexpr (DT == DT_F32) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) w[k] = __float_as_uint(v[k]);
+    } else if constexpr (N == 1) {
+        unsigned short h = (DT == DT_BF16) ? __bfloat16_as_ushort(__float2bfloat16_rn(v[0]))
+                                           : __half_as_ushort(__float2half_rn(v[0]));
+        w[0] = h;
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) {
+            uint32_t lo, hi;
+            if constexpr (DT == DT_BF16) {
+                lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[k]));
+                hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[k + 1]));
+            } else {
+                lo = __half_as_ushort(__float2half_rn(v[k]));
+                hi = __half_as_ushort(__float2half_rn(v[k + 1]));
+            }
+            w[k >> 1] = lo | (hi << 16);
+        }
+    }
+    char* p = reinterpret_cast<char*>(base) + idx * dt_bytes(DT);
+    if constexpr (TB >= 16) {
+#pragma unroll
+        for (int q = 0; q < TB / 16; ++q)
+            __stcs(reinterpret_cast<uint4*>(p) + q, make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]));
+    } else if constexpr (TB == 8) {
+        __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+    } else if constexpr (TB == 4) {
+        __stcs(reinterpret_cast<unsigned int*>(p), w[0]);
+    } else {
+        *reinterpret_cast<unsigned short*>(p) = (unsigned short)w[0];
+    }
+}
+
+// Lane group of G lanes inside a warp.
+template <int G>
+struct Group {
+    int gl;          // lane within the group
+    unsigned mask;   // members, for *_sync intrinsics
+    __device__ __forceinline__ Group()
+    {
+        const int lane = threadIdx.x & 31;
+        gl = lane & (G - 1);
+        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    }
+};
+
+// ----------------------------------------------------------------------------
+// Kernel arguments
+// ----------------------------------------------------------------------------
+struct SddmmArgs {
+    int64_t M, N, nnz;
+    int32_t K;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const int32_t* rowidx;    // COO row of every nonzero (balanced schedule only)
+    const float* vals;        // NULL = ones
+    const float* vals2;       // NULL = ones
+    const void* A; int64_t lda; const float* a_scale;
+    const void* B; int64_t ldb; const float* b_scale;
+    float* out;
+    const int2* bnd;          // chunk boundaries (row, nonzero); NULL = row-split
+    int64_t nchunks;
+};
+
+struct SpmmArgs {
+    int64_t M, N;
+    int32_t K;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const int32_t* rowidx;
+    const int32_t* vperm;     // values index through this permutation (S^T), or NULL
+    const float* vals;
+    const float* vals2;
+    const void* B; int64_t ldb; const float* b_scale;
+    void* C; int64_t ldc; int32_t dtc; int32_t accumulate;
+    const int2* bnd;          // NULL = row-split
+    const int4* meta;         // {head slot, tail slot, last row, unused} per chunk
+    const int32_t* head_s0;   // first slot of the split row a chunk's head piece belongs to
+    const int32_t* slot_np;   // pieces of the split row starting at a slot
+    int32_t* cnt;             // arrival counters per split row (self-resetting)
+    float* carry;             // partial rows, K floats per slot
+    int64_t nchunks;
+};
+
+// Kernel shape: lanes per group, 16-byte vectors per lane, nonzeros in flight.
+struct Shape { int G, NV, U; };
+
+// Shapes compiled into the library, indexed by position.
+#define SPK_SHAPES(X) \
+    X(0, 4, 1, 4)     \
+    X(1, 8, 1, 8)     \
+    X(2, 16, 1, 8)    \
+    X(3, 32, 1, 8)    \
+    X(4, 8, 2, 8)     \
+    X(5, 16, 2, 8)    \
+    X(6, 32, 2, 4)    \
+    X(7, 4, 2, 4)     \
+    X(8, 32, 4, 4)    \
+    X(9, 16, 1, 4)    \
+    X(10, 8, 2, 4)
+
+constexpr int kNumShapes = 11;
+int shape_index(int G, int NV, int U);   // -1 if not compiled
+Shape shape_at(int i);
+
+struct Launch {
+    int shape;         // index into SPK_SHAPES
+    bool vec;          // 16-byte vector mode (else one element per lane slot)
+    int threads;
+    bool chunks;       // balanced schedule
+};
+
+// Launchers (one per dtype family; defined in the sddmm_*.cu / spmm_*.cu files).
+cudaError_t launch_sddmm(int dta, int dtb, const Launch& L, const SddmmArgs& a, cudaStream_t s);
+cudaError_t launch_spmm(int dtb, const Launch& L, const SpmmArgs& a, cudaStream_t s);
+
+cudaError_t launch_sddmm_f32(int dta, const Launch& L, const SddmmArgs& a, cudaStream_t s);
+cudaError_t launch_sddmm_bf16(int dta, const Launch& L, const SddmmArgs& a, cudaStream_t s);
+cudaError_t launch_sddmm_f16(int dta, const Launch& L, const SddmmArgs& a, cudaStream_t s);
+cudaError_t launch_sddmm_e4m3(int dta, const Launch& L, const SddmmArgs& a, cudaStream_t s);
+cudaError_t launch_spmm_f32(const Launch& L, const SpmmArgs& a, cudaStream_t s);
+cudaError_t launch_spmm_bf16(const Launch& L, const SpmmArgs& a, cudaStream_t s);
+cudaError_t launch_spmm_f16(const Launch& L, const SpmmArgs& a, cudaStream_t s);
+cudaError_t launch_spmm_e4m3(const Launch& L, const SpmmArgs& a, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// Schedule / plan helpers (schedule.cu, transpose.cu)
+// ----------------------------------------------------------------------------
+struct SchedLayout {
+    int64_t nchunks;
+    size_t rowidx, bnd, meta, head_s0, slot_np, cnt, pieces, scan_tmp, total;
+};
+SchedLayout sched_layout(int64_t M, int64_t nnz, int32_t W);
+size_t scan_temp_bytes(int64_t n);
+cudaError_t scan_exclusive_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);
+cudaError_t build_schedule(const int32_t* rowptr, int64_t M, int64_t nnz, int32_t W, char* storage,
+                           const SchedLayout& L, int64_t* npieces_out, cudaStream_t s);
+cudaError_t launch_validate(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
+                            int32_t* report, cudaStream_t s);
+
+struct TplanLayout {
+    size_t colptr, rowidx, perm, sched, total;          // storage
+    size_t keys0, keys1, vals0, vals1, hist, scan_tmp, temp_total;  // temp
+    int64_t nblocks;
+    int passes;
+    SchedLayout sl;
+};
+TplanLayout tplan_layout(int64_t M, int64_t N, int64_t nnz, int32_t W);
+cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
+                            char* storage, char* temp, const TplanLayout& L, cudaStream_t s);
+
+cudaError_t launch_cast(const float* x, int64_t n, int dt, void* out, cudaStream_t s);
+cudaError_t launch_quant_e4m3(const float* X, int64_t M, int64_t K, int64_t ldx, uint8_t* Q, int64_t ldq,
+                              float* scales, cudaStream_t s);
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace spk
+
+// Host-side handle types (opaque in the C header).
+struct spk_csr_s {
+    int64_t M, N, nnz;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const int32_t* vperm;     // set for the transposed pattern of a plan
+    // balanced schedule (in caller storage)
+    bool has_sched;
+    int32_t W;
+    int64_t nchunks, npieces;
+    const int32_t* rowidx;
+    const int2* bnd;
+    const int4* meta;
+    const int32_t* head_s0;
+    const int32_t* slot_np;
+    int32_t* cnt;
+};
+
+struct spk_tplan_s {
+    spk_csr_s St;             // pattern of S^T (rowptr = colptr, colidx = rowidx), vperm = perm
+    const int32_t* colptr;
+    const int32_t* rowidx;
+    const int32_t* perm;
+    int64_t M, N;             // of S
+};

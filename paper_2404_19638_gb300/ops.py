@@ -1,0 +1,156 @@
+"""The compute entry points: SDDMM (Eq. 1), SpMM (Eq. 2), SpMM^T, and the
+precision kernels, as thin wrappers over libspk (argument marshalling only;
+every step runs in the library's CUDA kernels)."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from .binding import SPK_BF16, SPK_E4M3, SPK_F16, SPK_F32, Tune, check, lib
+from .sparse import CSR, TransposePlan, _stream
+
+_DT = {torch.float32: SPK_F32, torch.bfloat16: SPK_BF16, torch.float16: SPK_F16,
+       torch.float8_e4m3fn: SPK_E4M3, torch.uint8: SPK_E4M3}
+_OUT_DT = {torch.float32: SPK_F32, torch.bfloat16: SPK_BF16, torch.float16: SPK_F16}
+
+
+def _dense(X: torch.Tensor, name: str, device) -> tuple[int, int]:
+    if X.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if X.device != device:
+        raise ValueError(f"{name} is on {X.device}, the pattern on {device}")
+    if X.dtype not in _DT:
+        raise TypeError(f"{name}: unsupported dtype {X.dtype}")
+    if X.stride(1) != 1 and X.size(1) > 1:
+        raise ValueError(f"{name} must be row-major with unit column stride")
+    ld = X.stride(0) if X.size(0) > 1 else max(X.size(1), 1)
+    return _DT[X.dtype], ld
+
+
+def _vals(v, S, name):
+    if v is None:
+        return None
+    if v.dtype != torch.float32 or v.device != S.device or v.numel() != S.nnz:
+        raise ValueError(f"{name} must be a float32 tensor of length nnz on the pattern's device")
+    return v.contiguous()
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _tune(t):
+    t = Tune.make(t)
+    return None if t is None else ctypes.byref(t)
+
+
+def _scale(s, n, name, device):
+    if s is None:
+        return None
+    if s.dtype != torch.float32 or s.numel() != n or s.device != device:
+        raise ValueError(f"{name} must be float32 with one entry per row")
+    return s.contiguous()
+
+
+def sddmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, vals2=None, *, a_scale=None, b_scale=None,
+          out: torch.Tensor | None = None, tune=None, use_default_vals: bool = True) -> torch.Tensor:
+    """out_e = s_e * <A[i,:], B[j,:]> for every stored e = (i, j).  FP32, length nnz."""
+    if vals is None and use_default_vals:
+        vals = S.vals
+    dta, lda = _dense(A, "A", S.device)
+    dtb, ldb = _dense(B, "B", S.device)
+    if A.size(0) != S.M or B.size(0) != S.N or A.size(1) != B.size(1):
+        raise ValueError(f"shapes: S {S.M}x{S.N}, A {tuple(A.shape)}, B {tuple(B.shape)}")
+    K = A.size(1)
+    if out is None:
+        out = torch.empty(S.nnz, dtype=torch.float32, device=S.device)
+    vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
+    a_scale = _scale(a_scale, S.M, "a_scale", S.device)
+    b_scale = _scale(b_scale, S.N, "b_scale", S.device)
+    check(lib().spk_sddmm(S.handle, _ptr(vals), _ptr(vals2), dta, A.data_ptr(), lda, _ptr(a_scale), dtb,
+                          B.data_ptr(), ldb, _ptr(b_scale), K, out.data_ptr(), _tune(tune), _stream(S.device)),
+          "spk_sddmm")
+    return out
+
+
+def spmm(S: CSR, B: torch.Tensor, vals=None, vals2=None, *, b_scale=None, out: torch.Tensor | None = None,
+         out_dtype=torch.float32, accumulate: bool = False, tune=None, use_default_vals: bool = True) -> torch.Tensor:
+    """C = S B (or C += S B with accumulate=True).  C is M x K."""
+    if vals is None and use_default_vals:
+        vals = S.vals
+    dtb, ldb = _dense(B, "B", S.device)
+    if B.size(0) != S.N:
+        raise ValueError(f"B has {B.size(0)} rows, S has {S.N} columns")
+    K = B.size(1)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs an output tensor")
+        out = torch.empty((S.M, K), dtype=out_dtype, device=S.device)
+    dtc, ldc = _dense(out, "out", S.device)
+    if out.dtype not in _OUT_DT or out.shape != (S.M, K):
+        raise ValueError("out must be M x K in float32, bfloat16 or float16")
+    vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
+    b_scale = _scale(b_scale, S.N, "b_scale", S.device)
+    t = Tune.make(tune)
+    ws = S.workspace(K) if (S.has_schedule and (t is None or t.variant in (0, 2))) else None
+    check(lib().spk_spmm(S.handle, _ptr(vals), _ptr(vals2), dtb, B.data_ptr(), ldb, _ptr(b_scale), K, dtc,
+                         out.data_ptr(), ldc, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
+                         None if t is None else ctypes.byref(t), _stream(S.device)), "spk_spmm")
+    return out
+
+
+def spmm_t(S: CSR, Y: torch.Tensor, vals=None, vals2=None, *, y_scale=None, out: torch.Tensor | None = None,
+           out_dtype=torch.float32, accumulate: bool = False, tune=None, plan: TransposePlan | None = None,
+           use_default_vals: bool = True) -> torch.Tensor:
+    """X = S^T Y (N x K) through the transpose plan of S (built on first use)."""
+    if vals is None and use_default_vals:
+        vals = S.vals
+    P = plan or S.transpose_plan()
+    dty, ldy = _dense(Y, "Y", S.device)
+    if Y.size(0) != S.M:
+        raise ValueError(f"Y has {Y.size(0)} rows, S has {S.M} rows")
+    K = Y.size(1)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs an output tensor")
+        out = torch.empty((S.N, K), dtype=out_dtype, device=S.device)
+    dtx, ldx = _dense(out, "out", S.device)
+    if out.dtype not in _OUT_DT or out.shape != (S.N, K):
+        raise ValueError("out must be N x K in float32, bfloat16 or float16")
+    vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
+    y_scale = _scale(y_scale, S.M, "y_scale", S.device)
+    t = Tune.make(tune)
+    ws = P.workspace(K) if (t is None or t.variant in (0, 2)) else None
+    check(lib().spk_spmm_t(P.handle, _ptr(vals), _ptr(vals2), dty, Y.data_ptr(), ldy, _ptr(y_scale), K, dtx,
+                           out.data_ptr(), ldx, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
+                           None if t is None else ctypes.byref(t), _stream(S.device)), "spk_spmm_t")
+    return out
+
+
+def cast(x: torch.Tensor, dtype) -> torch.Tensor:
+    """Round-to-nearest-even cast of an FP32 tensor to bfloat16 / float16."""
+    if x.dtype != torch.float32 or not x.is_cuda:
+        raise TypeError("cast expects a float32 CUDA tensor")
+    if dtype not in (torch.bfloat16, torch.float16):
+        raise TypeError("cast target must be bfloat16 or float16")
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=dtype, device=x.device)
+    check(lib().spk_cast(x.data_ptr(), x.numel(), _DT[dtype], out.data_ptr(), _stream(x.device)), "spk_cast")
+    return out
+
+
+def quantize_e4m3_rows(X: torch.Tensor):
+    """Per-row E4M3 codes (torch.float8_e4m3fn) and FP32 scales (amax/448)."""
+    if X.dtype != torch.float32 or X.dim() != 2 or not X.is_cuda:
+        raise TypeError("quantize_e4m3_rows expects a 2-D float32 CUDA tensor")
+    X = X.contiguous()
+    M, K = X.shape
+    Q = torch.empty((M, K), dtype=torch.float8_e4m3fn, device=X.device)
+    scales = torch.empty(M, dtype=torch.float32, device=X.device)
+    check(lib().spk_quantize_e4m3_rows(X.data_ptr(), M, K, K, Q.data_ptr(), K, scales.data_ptr(),
+                                       _stream(X.device)), "spk_quantize_e4m3_rows")
+    return Q, scales
+
+
+__all__ = ["sddmm", "spmm", "spmm_t", "cast", "quantize_e4m3_rows"]

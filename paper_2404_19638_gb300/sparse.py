@@ -1,0 +1,204 @@
+"""Sparse pattern handles: CSR pattern + balanced schedule + transpose plan.
+
+PyTorch provides the device memory (the library never allocates): the
+schedule, the transpose plan and SpMM carry workspaces are ``torch.uint8``
+CUDA tensors owned by these objects.  All pattern-dependent setup happens
+once (Sec. 5.1: the pattern is fixed while the values change).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from .binding import SpkError, check, lib
+
+DEFAULT_CHUNK_WORK = 512
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _buffer(nbytes: int, device) -> torch.Tensor:
+    # the caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _as_i32(x, device) -> torch.Tensor:
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32))
+    x = x.to(device=device, dtype=torch.int32)
+    return x.contiguous()
+
+
+class CSR:
+    """Pattern of an M x N sparse matrix S (Sec. 3.1), optionally with values.
+
+    ``rowptr``/``colidx`` are int32 (numpy or torch); they are moved to
+    ``device`` once.  ``vals`` (FP32, length nnz, or None for all ones) is the
+    default value array of calls that do not pass their own.
+    """
+
+    def __init__(self, rowptr, colidx, shape, vals=None, *, device="cuda", schedule: bool = True,
+                 chunk_work: int = DEFAULT_CHUNK_WORK):
+        self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.M, self.N = int(shape[0]), int(shape[1])
+        self.rowptr = _as_i32(rowptr, self.device)
+        self.colidx = _as_i32(colidx, self.device)
+        if self.rowptr.numel() != self.M + 1:
+            raise ValueError("rowptr must have M + 1 entries")
+        self.nnz = int(self.colidx.numel())
+        self.vals = None if vals is None else torch.as_tensor(vals, dtype=torch.float32).to(self.device).contiguous()
+        self._h = ctypes.c_void_p()
+        check(lib().spk_csr_create(ctypes.byref(self._h), self.M, self.N, self.nnz, self.rowptr.data_ptr(),
+                                   self.colidx.data_ptr() if self.nnz else None), "spk_csr_create")
+        self._sched = None
+        self._ws = {}
+        self._tplan = None
+        if schedule:
+            self.build_schedule(chunk_work)
+
+    # ---------------------------------------------------------------- setup
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def build_schedule(self, chunk_work: int = DEFAULT_CHUNK_WORK) -> None:
+        nbytes = ctypes.c_size_t()
+        check(lib().spk_schedule_size(self._h, int(chunk_work), ctypes.byref(nbytes)), "spk_schedule_size")
+        storage = _buffer(nbytes.value, self.device)
+        with torch.cuda.device(self.device):
+            check(lib().spk_schedule_build(self._h, int(chunk_work), storage.data_ptr(), storage.numel(),
+                                           _stream(self.device)), "spk_schedule_build")
+        self._sched = storage
+        self._ws.clear()
+
+    @property
+    def has_schedule(self) -> bool:
+        return self._sched is not None
+
+    def schedule_info(self) -> dict:
+        nc, npc, w = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        check(lib().spk_schedule_info(self._h, ctypes.byref(nc), ctypes.byref(npc), ctypes.byref(w)),
+              "spk_schedule_info")
+        return {"nchunks": nc.value, "npieces": npc.value, "chunk_work": w.value}
+
+    def schedule_bounds(self) -> torch.Tensor:
+        """(nchunks + 1) x 2 int32 boundaries (row, nonzero) of the schedule."""
+        n = self.schedule_info()["nchunks"] + 1
+        out = torch.empty((n, 2), dtype=torch.int32, device=self.device)
+        check(lib().spk_schedule_bounds(self._h, out.data_ptr(), _stream(self.device)), "spk_schedule_bounds")
+        return out
+
+    def merge_path_points(self, W: int, n: int) -> torch.Tensor:
+        """Raw merge-path split points at diagonals 0, W, ..., n*W (clamped)."""
+        out = torch.empty((n + 1, 2), dtype=torch.int32, device=self.device)
+        check(lib().spk_merge_path_points(self._h, int(W), int(n), out.data_ptr(), _stream(self.device)),
+              "spk_merge_path_points")
+        return out
+
+    def validate(self) -> dict:
+        """Device check of the CSR invariants; synchronises."""
+        rep = torch.empty(4, dtype=torch.int32, device=self.device)
+        check(lib().spk_csr_validate(self._h, rep.data_ptr(), _stream(self.device)), "spk_csr_validate")
+        r = rep.cpu().tolist()
+        return {"error": r[0], "first_bad": r[1], "bad_count": r[2], "unsorted": bool(r[3])}
+
+    def workspace(self, K: int) -> torch.Tensor | None:
+        """Carry workspace of an SpMM with K columns (cached per K)."""
+        nbytes = ctypes.c_size_t()
+        check(lib().spk_spmm_workspace_size(self._h, int(K), ctypes.byref(nbytes)), "spk_spmm_workspace_size")
+        if nbytes.value == 0:
+            return None
+        ws = self._ws.get(K)
+        if ws is None or ws.numel() < nbytes.value:
+            ws = _buffer(nbytes.value, self.device)
+            self._ws[K] = ws
+        return ws
+
+    def transpose_plan(self, chunk_work: int = DEFAULT_CHUNK_WORK) -> "TransposePlan":
+        if self._tplan is None or self._tplan.chunk_work != chunk_work:
+            self._tplan = TransposePlan(self, chunk_work)
+        return self._tplan
+
+    def tune_default(self, op: int, dtype_code: int, K: int) -> dict:
+        from .binding import Tune
+        t = Tune()
+        check(lib().spk_tune_default(self._h, int(op), int(dtype_code), int(K), ctypes.byref(t)), "spk_tune_default")
+        return t.as_dict()
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().spk_csr_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def __repr__(self):
+        return f"CSR(M={self.M}, N={self.N}, nnz={self.nnz}, schedule={self.has_schedule})"
+
+
+class TransposePlan:
+    """CSC of S (the CSR of S^T) with the slot permutation, built on the device."""
+
+    def __init__(self, S: CSR, chunk_work: int = DEFAULT_CHUNK_WORK):
+        self.S = S
+        self.chunk_work = chunk_work
+        self.M, self.N, self.nnz = S.M, S.N, S.nnz
+        st, tmp = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().spk_tplan_size(S.handle, int(chunk_work), ctypes.byref(st), ctypes.byref(tmp)), "spk_tplan_size")
+        self._storage = _buffer(st.value, S.device)
+        temp = _buffer(tmp.value, S.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(S.device):
+            check(lib().spk_tplan_build(S.handle, int(chunk_work), self._storage.data_ptr(), self._storage.numel(),
+                                        temp.data_ptr(), temp.numel(), ctypes.byref(self._h), _stream(S.device)),
+                  "spk_tplan_build")
+        del temp
+        self._ws = {}
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def arrays(self):
+        """(colptr, rowidx, perm) as int32 CUDA tensors (views of the plan storage)."""
+        cp, ri, pm = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        check(lib().spk_tplan_arrays(self._h, ctypes.byref(cp), ctypes.byref(ri), ctypes.byref(pm)),
+              "spk_tplan_arrays")
+        base = self._storage.data_ptr()
+
+        def view(ptr, n):
+            off = ptr.value - base
+            return self._storage[off:off + 4 * n].view(torch.int32)
+
+        return view(cp, self.N + 1), view(ri, self.nnz), view(pm, self.nnz)
+
+    def workspace(self, K: int) -> torch.Tensor | None:
+        nbytes = ctypes.c_size_t()
+        check(lib().spk_spmm_t_workspace_size(self._h, int(K), ctypes.byref(nbytes)), "spk_spmm_t_workspace_size")
+        if nbytes.value == 0:
+            return None
+        ws = self._ws.get(K)
+        if ws is None or ws.numel() < nbytes.value:
+            ws = _buffer(nbytes.value, self.S.device)
+            self._ws[K] = ws
+        return ws
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().spk_tplan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+__all__ = ["CSR", "TransposePlan", "SpkError", "DEFAULT_CHUNK_WORK"]
