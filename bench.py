@@ -1,0 +1,397 @@
+"""Throughput of the local SDDMM + SpMM step on GB300.
+
+A step is one pass of the hot path over one batch of input: out = SDDMM(S, A, B)
+(Eq. 1) followed by C = SpMM(S, B) (Eq. 2) on the power-law workload (R-MAT
+scale 20, edge factor 16, K = 64, FP32), inputs resident in HBM, L2 flushed
+between steps.  Metric: GFLOP/s = 2 * (2 * nnz * K) / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload rmat20|tiny|rec|gnn] [--dtype f32|bf16]
+
+Prints one JSON line (rank 0).  With torchrun, every rank runs an independent
+replica on its own GPU (the step has no data exchange) and the line reports
+the aggregate over ranks, timed by the slowest rank.
+
+--impl reference times the FP64 CPU oracle (the reference of this build) on a
+bounded row sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "SDDMM+SpMM GFLOP/s (2*nnz*K per op)"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+def load_workload(name: str):
+    if name == "rmat20":
+        P = synth.rmat_problem(20, 16, 64, seed=0)
+        desc = ("rmat20: R-MAT scale 20 (1,048,576 x 1,048,576), edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+                "duplicates removed, values U[-1,1]; A, B 2^20 x 64 N(0,1)")
+    elif name == "tiny":
+        P = synth.tiny(seed=0)
+        desc = "tiny: 4096 x 4096, 16 distinct uniform columns per row, values U[-1,1]; A, B 4096 x 32 U[-1,1]"
+    elif name == "rec":
+        P = synth.rec(seed=0)
+        desc = ("rec: 2,000,000 x 500,000 Chung-Lu, Zipf(1.1) weights clipped to [1,20000], 50,000,000 nnz, "
+                "values U{1..5}; A 2M x 128, B 500K x 128 N(0,1)")
+    elif name == "gnn":
+        P = synth.gnn(seed=0)
+        P.vals = None
+        desc = "gnn: R-MAT scale 22, edge factor 8, unit values; A = B = H 2^22 x 64 N(0,0.1)"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return P, desc
+
+
+def algorithmic_bytes(P, elt: int) -> dict:
+    """Compulsory HBM bytes per launch: every input read once, every output
+    written once (index arrays int32, values FP32, factors `elt` bytes)."""
+    M, N, K, nnz = P.M, P.N, P.K, P.nnz
+    sddmm = 4 * (M + 1) + 4 * nnz + 4 * nnz + M * K * elt + N * K * elt + 4 * nnz
+    spmm = 4 * (M + 1) + 8 * nnz + N * K * elt + M * K * 4
+    return {"sddmm": sddmm, "spmm": spmm}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d.get("bf16_tflops", 0))}, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2404_19638_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, dtype: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"sddmm_spmm_{workload}_{dtype}.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"^traffic_per_launch:\s*(\{.*\})\s*$", open(path).read(), flags=re.M)
+    if not m:
+        return None
+    d = json.loads(m.group(1))
+    if d.get("source_sha") != kernel_sources_sha():
+        return None
+    return d
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample_rows(P, step: int, target_nnz: int):
+    """Every stride-th row starting at `step % stride`: a bounded, stratified
+    sample over the whole matrix (heavy rows at the top included in turn)."""
+    stride = max(1, int(round(P.nnz / max(target_nnz, 1))))
+    rows = np.arange(step % stride, P.M, stride, dtype=np.int64)
+    nnz = int(np.diff(P.rowptr.astype(np.int64))[rows].sum())
+    return rows, nnz, stride
+
+
+def time_oracle_step(P, rows):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals, rows=rows)
+    oracle.spmm(P.rowptr, P.colidx, P.B, P.vals, rows=rows)
+    return time.perf_counter() - t0
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    P, desc = load_workload(args.workload)
+    import oracle
+    oracle.build()
+    target = args.ref_nnz
+    times, flops = [], []
+    for s in range(args.warmup + args.steps):
+        rows, nnz, stride = oracle_sample_rows(P, s, target)
+        t = time_oracle_step(P, rows)
+        if s >= args.warmup:
+            times.append(t)
+            flops.append(2.0 * 2.0 * nnz * P.K)
+    T = sum(times)
+    value = sum(flops) / T / 1e9
+    sample = (f"per step: rows i = s mod {stride} (every {stride}-th row, ~{target:,} of {P.nnz:,} nonzeros), "
+              f"SDDMM + SpMM in the FP64 oracle, single thread")
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "M": P.M, "N": P.N, "K": P.K, "nnz": P.nnz},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def main(args):
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2404_19638_gb300 as spk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    P, desc = load_workload(args.workload)
+    K = P.K
+    dt = torch.float32 if args.dtype == "f32" else torch.bfloat16
+    elt = 4 if args.dtype == "f32" else 2
+    vals = None if P.vals is None else torch.from_numpy(P.vals).to(dev)
+    S = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), vals, device=dev, chunk_work=args.chunk_work)
+    A32 = torch.from_numpy(P.A).to(dev)
+    B32 = A32 if P.B is P.A else torch.from_numpy(P.B).to(dev)
+    A = A32 if dt == torch.float32 else spk.cast(A32, dt)
+    B = B32 if dt == torch.float32 else (A if P.B is P.A else spk.cast(B32, dt))
+    out = torch.empty(P.nnz, dtype=torch.float32, device=dev)
+    C = torch.empty((P.M, K), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # > 129 MB L2
+    tune_sd = json.loads(args.tune_sddmm) if args.tune_sddmm else None
+    tune_sp = json.loads(args.tune_spmm) if args.tune_spmm else None
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        spk.sddmm(S, A, B, out=out, tune=tune_sd)
+        ev[1].record(stream)
+        spk.spmm(S, B, out=C, tune=tune_sp)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step()
+    torch.cuda.synchronize(dev)
+
+    events = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    with ClockSampler(dev.index if world == 1 else local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            step()
+            ev[2].record(stream)
+            events.append(ev)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    t_sd = [e[0].elapsed_time(e[1]) for e in events]
+    t_sp = [e[1].elapsed_time(e[2]) for e in events]
+    T = (sum(t_sd) + sum(t_sp)) / 1e3                      # seconds, this rank
+    if world > 1:
+        tt = torch.tensor([T], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        T = float(tt.item())
+    flops_step = 2.0 * 2.0 * P.nnz * K
+    value = world * flops_step * args.steps / T / 1e9
+
+    # end to end through the public API: pinned host inputs in, results out
+    hA = torch.from_numpy(P.A).pin_memory()
+    hB = hA if P.B is P.A else torch.from_numpy(P.B).pin_memory()
+    hv = None if P.vals is None else torch.from_numpy(P.vals).pin_memory()
+    hout = torch.empty(P.nnz, dtype=torch.float32).pin_memory()
+    hC = torch.empty((P.M, K), dtype=torch.float32).pin_memory()
+    dA = torch.empty_like(A32); dB = dA if P.B is P.A else torch.empty_like(B32)
+    dv = None if hv is None else torch.empty_like(vals)
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        if dB is not dA:
+            dB.copy_(hB, non_blocking=True)
+        if dv is not None:
+            dv.copy_(hv, non_blocking=True)
+        a = dA if dt == torch.float32 else spk.cast(dA, dt)
+        b = dB if dt == torch.float32 else (a if dB is dA else spk.cast(dB, dt))
+        spk.sddmm(S, a, b, dv, out=out, tune=tune_sd)
+        spk.spmm(S, b, dv, out=C, tune=tune_sp)
+        hout.copy_(out, non_blocking=True)
+        hC.copy_(C, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(3, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    Te = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([Te], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        Te = float(tt.item())
+    h2d = (hA.numel() * 4 + (0 if hB is hA else hB.numel() * 4) + (0 if hv is None else hv.numel() * 4))
+    d2h = hout.numel() * 4 + hC.numel() * 4
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    ab = algorithmic_bytes(P, elt)
+    ms_sd, ms_sp = statistics.mean(t_sd), statistics.mean(t_sp)
+    dom = "sddmm" if ms_sd >= ms_sp else "spmm"
+    ms_dom = ms_sd if dom == "sddmm" else ms_sp
+    achieved = ab[dom] / (ms_dom / 1e3) / 1e9
+    traffic = profiled_traffic(args.workload, args.dtype)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": desc, "M": P.M, "N": P.N, "K": K, "nnz": P.nnz, "op": "SDDMM then SpMM",
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "chunk_work": args.chunk_work, "parallelism": "replicas" if world > 1 else "single GPU"},
+        "kernels": {"sddmm_ms": ms_sd, "spmm_ms": ms_sp,
+                    "sddmm_gflops": 2.0 * P.nnz * K / (ms_sd / 1e3) / 1e9,
+                    "spmm_gflops": 2.0 * P.nnz * K / (ms_sp / 1e3) / 1e9,
+                    "sddmm_algo_gbs": ab["sddmm"] / (ms_sd / 1e3) / 1e9,
+                    "spmm_algo_gbs": ab["spmm"] / (ms_sp / 1e3) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind,
+                     "algorithmic_bytes": ab[dom],
+                     "traffic": None if traffic is None else traffic.get(dom)},
+        "e2e": {"value": world * flops_step * e2e_steps / Te / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "wall_s": wall,
+    }
+    summ = clk.summary()
+    line["clocks"] = summ
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rows, nnz, stride = oracle_sample_rows(P, 0, args.cpu_nnz)
+        t = time_oracle_step(P, rows)
+        line["cpu_baseline"] = {"value": 2.0 * 2.0 * nnz * K / t / 1e9, "unit": "GFLOP/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"every {stride}-th row ({nnz:,} of {P.nnz:,} nonzeros), SDDMM + SpMM "
+                                          f"in the FP64 oracle on one host core, {t:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--chunk-work", type=int, default=512)
+    ap.add_argument("--tune-sddmm", default=None, help='JSON spk_tune fields, e.g. {"group_lanes": 8}')
+    ap.add_argument("--tune-spmm", default=None)
+    ap.add_argument("--cpu-nnz", type=int, default=2_000_000, help="nonzeros in the CPU-baseline sample")
+    ap.add_argument("--ref-nnz", type=int, default=500_000, help="nonzeros per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    return a
+
+
+if __name__ == "__main__":
+    sys.exit(main(parse()))

@@ -225,9 +225,10 @@ struct Shape { int G, NV, U; };
     X(7, 4, 2, 4)     \
     X(8, 32, 4, 4)    \
     X(9, 16, 1, 4)    \
-    X(10, 8, 2, 4)
+    X(10, 8, 2, 4)    \
+    X(11, 8, 1, 4)
 
-constexpr int kNumShapes = 11;
+constexpr int kNumShapes = 12;
 int shape_index(int G, int NV, int U);   // -1 if not compiled
 Shape shape_at(int i);
 
