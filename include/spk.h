@@ -90,7 +90,9 @@ spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int32_t K, spk_
 
 /* ------------------------------------------------------------- pattern -- */
 /* Wrap a CSR pattern (Sec. 3.1: S is M x N).  rowptr[M+1], colidx[nnz] are
- * borrowed device pointers that must outlive the handle.  No device work. */
+ * borrowed device pointers that must outlive the handle; colidx must be
+ * 16-byte aligned (it is streamed with 16-byte asynchronous copies).  No
+ * device work. */
 spk_status spk_csr_create(spk_csr* out, int64_t M, int64_t N, int64_t nnz,
                           const int32_t* rowptr, const int32_t* colidx);
 spk_status spk_csr_destroy(spk_csr S);

@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -27,6 +29,22 @@ int shape_index(int G, int NV, int U)
 }
 
 Shape shape_at(int i) { return kShapes[i]; }
+
+cudaError_t ensure_smem(const void* fn, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& have = done[{fn, dev}];
+    if (have >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 
 cudaError_t launch_sddmm(int dta, int dtb, const Launch& L, const SddmmArgs& a, cudaStream_t s)
 {
@@ -120,6 +138,7 @@ extern "C" spk_status spk_csr_create(spk_csr* out, int64_t M, int64_t N, int64_t
     REQUIRE(rowptr, SPK_ERR_ARG, "spk_csr_create: rowptr is NULL");
     REQUIRE(colidx || nnz == 0, SPK_ERR_ARG, "spk_csr_create: colidx is NULL");
     REQUIRE(nnz == 0 || N > 0, SPK_ERR_SHAPE, "spk_csr_create: nonzeros in a matrix with no columns");
+    REQUIRE(nnz == 0 || aligned16(colidx), SPK_ERR_ARG, "spk_csr_create: colidx must be 16-byte aligned");
     spk_csr_s* S = new (std::nothrow) spk_csr_s();
     REQUIRE(S, SPK_ERR_ARG, "spk_csr_create: out of host memory");
     S->M = M; S->N = N; S->nnz = nnz;
@@ -353,9 +372,10 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
         REQUIRE(aligned16(ws), SPK_ERR_WORKSPACE, "%s: workspace must be 16-byte aligned", name);
     }
     SpmmArgs a;
-    a.M = S->M; a.N = S->N; a.K = K;
+    a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = K;
     a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vperm = S->vperm;
     a.vals = vals; a.vals2 = vals2;
+    a.vals_staged = (vals && !vals2 && !S->vperm && aligned16(vals)) ? 1 : 0;
     a.B = B; a.ldb = ldb; a.b_scale = b_scale;
     a.C = C; a.ldc = ldc; a.dtc = dtc; a.accumulate = accumulate;
     a.bnd = L.chunks ? S->bnd : nullptr;

@@ -25,38 +25,44 @@ struct BatchDesc {
 };
 
 // (G, NV, U) shapes available to batched items; class = dtype * 8 + position
-// in this list.  Each (op, class) routine is a separate non-inlined function,
-// so the merged kernel's register count is the largest routine's (capped at
-// 128 for two resident CTAs per SM); BF16 uses only the U = 4, NV = 1 shapes,
-// which fit that budget without spilling.
+// in this list.  Each (op, class) routine is a separate non-inlined function;
+// every warp owns a fixed shared-memory region big enough for any of them.
 #define SPK_BATCH_SHAPES(X) \
     X(0, 4, 1, 4)           \
     X(1, 8, 1, 4)           \
-    X(2, 8, 1, 8)           \
-    X(3, 16, 1, 4)          \
-    X(4, 16, 2, 4)
+    X(2, 16, 1, 4)
 
-constexpr int kBatchShapes = 5;
+constexpr int kBatchShapes = 3;
 static const Shape kBatchShapeList[kBatchShapes] = {
 #define X(i, G_, NV_, U_) {G_, NV_, U_},
     SPK_BATCH_SHAPES(X)
 #undef X
 };
 
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// Shared-memory words of one warp: the largest ring of any batched shape
+// (an SDDMM group also keeps A slices; one 16-byte vector per lane).
+constexpr int kWarpWords = cmax(cmax((32 / 4) * pipe_words(4, 1, 4, 1), (32 / 8) * pipe_words(8, 1, 4, 1)),
+                                (32 / 16) * pipe_words(16, 1, 4, 1));
+constexpr int kBatchThreads = 128;
+constexpr size_t kBatchSmem = (size_t)(kBatchThreads / 32) * kWarpWords * sizeof(int);
+
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit)
+__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit, int* warp_sm)
 {
     const Group<G> g;
+    int* sm = warp_sm + ((threadIdx.x & 31) / G) * pipe_words(G, NV, U, NV);
     const int64_t c = unit * (32 / G) + ((threadIdx.x & 31) / G);
     if (c >= a.nchunks) return;
     const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-    sddmm_span<DT, DT, vec_elems(DT), G, NV, U, false>(a, g, b0.x, b0.y, b1.y);
+    sddmm_span_pipe<DT, DT, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y);
 }
 
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb)
+__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb, int* warp_sm)
 {
     const Group<G> g;
+    int* sm = warp_sm + ((threadIdx.x & 31) / G) * pipe_words(G, NV, U, 0);
     const int kb = (int)(unit % nkb);
     const int64_t c = (unit / nkb) * (32 / G) + ((threadIdx.x & 31) / G);
     if (c >= a.nchunks) return;
@@ -64,13 +70,15 @@ __device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, in
     const int4 m = a.meta[c];
     if (b1.y == b0.y && m.z < b0.x) return;
     const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-    spmm_span<DT, vec_elems(DT), G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    spmm_span_pipe<DT, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
 }
 
-__global__ void __launch_bounds__(256, 2) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
+__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
                                                const int64_t* __restrict__ unit_begin, int64_t total_units,
                                                unsigned long long* counter, unsigned int* done)
 {
+    extern __shared__ int smem[];
+    int* warp_sm = smem + (threadIdx.x / 32) * kWarpWords;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long u = 0;
@@ -88,16 +96,16 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchDesc* __restrict__ 
         if (d.op == 0) {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local); break;              \
-    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local); break;
+    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local, warp_sm); break;              \
+    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local, warp_sm); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
         } else {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb); break;        \
-    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb); break;
+    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb, warp_sm); break;        \
+    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb, warp_sm); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
@@ -163,7 +171,7 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
         if (S->vperm) return bfail(SPK_ERR_ARG, where + "transposed patterns are not batched");
         if (!S->has_sched) return bfail(SPK_ERR_STATE, where + "pattern needs spk_schedule_build first");
         if (it.dt != SPK_F32 && it.dt != SPK_BF16) return bfail(SPK_ERR_DTYPE, where + "dtype must be F32 or BF16");
-        if (it.K < 1 || it.K > 128) return bfail(SPK_ERR_SHAPE, where + "K must be in [1, 128]");
+        if (it.K < 1) return bfail(SPK_ERR_SHAPE, where + "K must be >= 1");
         const int vecn = vec_elems(it.dt);
         if (it.K % vecn) return bfail(SPK_ERR_UNSUPPORTED, where + "K must be a multiple of 16 bytes of elements");
         if (it.ldb < it.K || (it.ldb * dt_bytes(it.dt)) % 16 || (reinterpret_cast<uintptr_t>(it.B) & 15))
@@ -183,16 +191,13 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
         }
         // shape
         const int nvec = it.K / vecn;
-        // Register budget of the merged kernel (2 CTAs of 256 threads per SM):
-        // BF16 rows (8 values per 16-byte vector) keep 4 nonzeros in flight.
-        const bool bf = (it.dt == SPK_BF16);
-        if (nvec > (bf ? 16 : 32))
-            return bfail(SPK_ERR_UNSUPPORTED, where + "batched K is limited to 128 (F32) / 128 (BF16)");
-        int G, NV, U;
-        if (nvec <= 4) { G = 4; NV = 1; U = 4; }
-        else if (nvec <= 8) { G = 8; NV = 1; U = bf ? 4 : 8; }
-        else if (nvec <= 16) { G = 16; NV = 1; U = 4; }
-        else { G = 16; NV = 2; U = 4; }
+        // Batched shapes: one K block of at most 16 vectors of 16 bytes
+        // (K <= 64 in FP32, <= 128 in BF16).
+        if (nvec > 16) return bfail(SPK_ERR_UNSUPPORTED, where + "batched K is limited to 16 vectors of 16 bytes");
+        int G, NV = 1, U = 4;
+        if (nvec <= 4) G = 4;
+        else if (nvec <= 8) G = 8;
+        else G = 16;
         if (it.tune) {
             if (it.tune->group_lanes) G = it.tune->group_lanes;
             if (it.tune->vecs_per_lane) NV = it.tune->vecs_per_lane;
@@ -201,7 +206,7 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
         int sidx = -1;
         for (int q = 0; q < kBatchShapes; ++q)
             if (kBatchShapeList[q].G == G && kBatchShapeList[q].NV == NV && kBatchShapeList[q].U == U) sidx = q;
-        if (sidx < 0 || (it.dt == SPK_BF16 && (sidx == 2 || sidx == 4)))
+        if (sidx < 0 || G * NV < nvec)
             return bfail(SPK_ERR_UNSUPPORTED, where + "shape not available in batched mode");
         BatchDesc& d = P.descs[m];
         d.op = it.op;
@@ -222,9 +227,10 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
         } else {
             d.nkb = (nvec + G * NV - 1) / (G * NV);
             SpmmArgs& a = d.sp;
-            a.M = S->M; a.N = S->N; a.K = it.K;
+            a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = it.K;
             a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vperm = nullptr;
             a.vals = it.vals; a.vals2 = nullptr;
+            a.vals_staged = (it.vals && (reinterpret_cast<uintptr_t>(it.vals) & 15u) == 0) ? 1 : 0;
             a.B = it.B; a.ldb = it.ldb; a.b_scale = nullptr;
             a.C = it.out; a.ldc = it.ldc; a.dtc = SPK_F32; a.accumulate = 0;
             a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
@@ -282,7 +288,8 @@ extern "C" spk_status spk_batch_create(const spk_batch_item* items, int32_t coun
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, 0);
+    if (e == cudaSuccess) e = ensure_smem((const void*)k_batch, kBatchSmem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem);
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
     spk_batch_s* B = new (std::nothrow) spk_batch_s();
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_create: out of host memory");
@@ -301,7 +308,7 @@ extern "C" spk_status spk_batch_run(spk_batch B, void* stream)
 {
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_run: handle is NULL");
     if (B->total_units == 0) return SPK_OK;
-    k_batch<<<B->grid, 256, 0, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
+    k_batch<<<B->grid, kBatchThreads, kBatchSmem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
                                                         B->d_counter, B->d_done);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_run: ") + cudaGetErrorString(e));

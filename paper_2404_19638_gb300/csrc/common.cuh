@@ -90,6 +90,65 @@ __device__ __forceinline__ void load_elems(const void* base, int64_t idx, float*
     }
 }
 
+// Raw (still packed) elements: gathered rows stay packed in registers while
+// their loads are in flight and are widened at the FMA, so a 16-byte vector
+// costs 4 registers whatever the dtype.
+template <int DT, int N>
+struct Raw {
+    static constexpr int TB = N * dt_bytes(DT);
+    static constexpr int NW = (TB + 3) / 4;
+    uint32_t w[NW];
+};
+
+template <int DT, int N>
+__device__ __forceinline__ void load_raw(const void* base, int64_t idx, Raw<DT, N>& r)
+{
+    constexpr int TB = Raw<DT, N>::TB;
+    const char* p = reinterpret_cast<const char*>(base) + idx * dt_bytes(DT);
+    if constexpr (TB >= 16) {
+#pragma unroll
+        for (int q = 0; q < TB / 16; ++q) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + q);
+            r.w[4 * q] = v.x; r.w[4 * q + 1] = v.y; r.w[4 * q + 2] = v.z; r.w[4 * q + 3] = v.w;
+        }
+    } else if constexpr (TB == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        r.w[0] = v.x; r.w[1] = v.y;
+    } else if constexpr (TB == 4) {
+        r.w[0] = __ldg(reinterpret_cast<const unsigned int*>(p));
+    } else if constexpr (TB == 2) {
+        r.w[0] = __ldg(reinterpret_cast<const unsigned short*>(p));
+    } else {
+        r.w[0] = __ldg(reinterpret_cast<const unsigned char*>(p));
+    }
+}
+
+template <int DT, int N>
+__device__ __forceinline__ void zero_raw(Raw<DT, N>& r)
+{
+#pragma unroll
+    for (int k = 0; k < Raw<DT, N>::NW; ++k) r.w[k] = 0u;
+}
+
+// Widen all N elements of a raw vector.
+template <int DT, int N>
+__device__ __forceinline__ void unpack_all(const Raw<DT, N>& r, float* out)
+{
+    if constexpr (DT == DT_E4M3 && N >= 2) {
+#pragma unroll
+        for (int k = 0; k < N; k += 2) {
+            const uint32_t x = r.w[k >> 2];
+            const __nv_fp8x2_storage_t q2 = (__nv_fp8x2_storage_t)((x >> (8 * (k & 3))) & 0xffffu);
+            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q2, __NV_E4M3);
+            const float2 f = __half22float2(__half2(hr));
+            out[k] = f.x; out[k + 1] = f.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) out[k] = unpack_one<DT>(r.w, k);
+    }
+}
+
 // Plain (coherent, L1-bypassing) load of C for accumulate and of the carry rows.
 template <int DT, int N>
 __device__ __forceinline__ void load_elems_cg(const void* base, int64_t idx, float* out)
@@ -159,6 +218,13 @@ __device__ __forceinline__ void store_elems(void* base, int64_t idx, const float
     }
 }
 
+// Resident 256-thread CTAs per SM a kernel is compiled for, from the
+// registers of gathered rows each lane keeps in flight (U x NV raw vectors).
+__host__ __device__ constexpr int min_ctas(int inflight_regs)
+{
+    return inflight_regs <= 16 ? 3 : (inflight_regs <= 32 ? 2 : 1);
+}
+
 // Lane group of G lanes inside a warp.
 template <int G>
 struct Group {
@@ -191,8 +257,9 @@ struct SddmmArgs {
 };
 
 struct SpmmArgs {
-    int64_t M, N;
+    int64_t M, N, nnz;
     int32_t K;
+    int32_t vals_staged;      // vals is 16-byte aligned and used alone: stream it with the indices
     const int32_t* rowptr;
     const int32_t* colidx;
     const int32_t* rowidx;
@@ -282,7 +349,13 @@ cudaError_t launch_cast(const float* x, int64_t n, int dt, void* out, cudaStream
 cudaError_t launch_quant_e4m3(const float* X, int64_t M, int64_t K, int64_t ldx, uint8_t* Q, int64_t ldq,
                               float* scales, cudaStream_t s);
 
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Opt a kernel into `bytes` of dynamic shared memory (needed above 48 KB);
+// remembered per kernel and device.
+cudaError_t ensure_smem(const void* fn, size_t bytes);
 
 }  // namespace spk
 

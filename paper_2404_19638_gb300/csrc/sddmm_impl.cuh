@@ -3,10 +3,12 @@
 // inner product).
 //
 // A lane group of G lanes walks a span of consecutive nonzeros U at a time:
-//   1. the U column indices (and COO rows) are read as broadcast loads,
-//   2. the U gathered rows of B and the A rows they meet are issued together
-//      (an A row is loaded only where the row changes inside the batch), so a
-//      batch keeps U*NV 16-byte loads in flight per lane,
+//   1. the column indices and COO rows of the span arrive through shared
+//      memory one tile ahead (cp.async, see tiles.cuh), so gathers never wait
+//      on index loads,
+//   2. the U gathered rows of B are issued together (U*NV 16-byte loads in
+//      flight per lane); the A slice of the current row stays in registers and
+//      is reloaded only where the row changes,
 //   3. each lane forms U partial dot products over its slice of K,
 //   4. a reduce-scatter across the group (U-1 shuffles plus log2(G/U)
 //      butterflies, instead of U*log2(G)) leaves the full sum for nonzero u in
@@ -15,159 +17,177 @@
 // long rows are cut into pieces; SDDMM outputs are per nonzero, so pieces
 // need no combining.
 #pragma once
-#include "common.cuh"
+#include "pipe.cuh"
 
 namespace spk {
 
 template <int DTA, int DTB, int VECN, int G, int NV, int U, bool KNOWN_ROW>
-__device__ __forceinline__ void sddmm_span(const SddmmArgs& a, const Group<G>& g, int64_t r0,
+__device__ __forceinline__ void sddmm_span(const SddmmArgs& a, const Group<G>& g, int* tiles, int64_t r0,
                                            int64_t e0, int64_t e1)
 {
+    constexpr int T = TileCfg<G>::T;
+    static_assert(T % U == 0, "tile must hold whole batches");
     const int nvec = a.K / VECN;               // vectors per dense row
     constexpr int PER_BLK = G * NV;
     const int nkb = (nvec + PER_BLK - 1) / PER_BLK;
-    float arow[NV][VECN];          // used when the span is one known row
-    bool have_arow = false;
+    float av[NV][VECN];                        // A slice of row `ra` (single K block only)
+    int ra = -1;
+    if (e0 >= e1) return;
 
-    for (int64_t eb = e0 & ~int64_t(U - 1); eb < e1; eb += U) {
-        int j[U], row[U];
-        bool ok[U];
+    const int64_t tb0 = e0 & ~int64_t(3);
+    const int32_t* rsrc = KNOWN_ROW ? nullptr : a.rowidx;
+    fill_tile<G>(tiles, 0, tb0, a.nnz, g.gl, a.colidx, rsrc, nullptr);
+    cp_async_commit();
+    int t = 0;
+    for (int64_t tb = tb0; tb < e1; tb += T, ++t) {
+        const int buf = t & 1;
+        if (tb + T < e1) fill_tile<G>(tiles, buf ^ 1, tb + T, a.nnz, g.gl, a.colidx, rsrc, nullptr);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp(g.mask);
+        const int* colt = tiles + buf * T;
+        const int* rowt = tiles + 2 * T + buf * T;
+        for (int b = 0; b < T; b += U) {
+            const int64_t eb = tb + b;
+            if (eb >= e1) break;
+            int j[U], row[U];
+            bool ok[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t e = eb + u;
-            ok[u] = (e >= e0) && (e < e1);
-            j[u] = ok[u] ? __ldg(a.colidx + e) : 0;
-            if constexpr (KNOWN_ROW) row[u] = (int)r0;
-            else row[u] = ok[u] ? __ldg(a.rowidx + e) : -1;
-        }
-        float p[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) p[u] = 0.f;
-
-        for (int kb = 0; kb < nkb; ++kb) {
-            float bv[U][NV][VECN];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    const int v = kb * PER_BLK + t * G + g.gl;
-                    if (ok[u] && v < nvec) {
-                        load_elems<DTB, VECN>(a.B, (int64_t)j[u] * a.ldb + (int64_t)v * VECN, bv[u][t]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) bv[u][t][q] = 0.f;
-                    }
+            for (int u = 0; u < U; u += 4) {
+                const int4 c4 = *reinterpret_cast<const int4*>(colt + b + u);
+                j[u] = c4.x; j[u + 1] = c4.y; j[u + 2] = c4.z; j[u + 3] = c4.w;
+                if constexpr (KNOWN_ROW) {
+                    row[u] = row[u + 1] = row[u + 2] = row[u + 3] = (int)r0;
+                } else {
+                    const int4 r4 = *reinterpret_cast<const int4*>(rowt + b + u);
+                    row[u] = r4.x; row[u + 1] = r4.y; row[u + 2] = r4.z; row[u + 3] = r4.w;
                 }
             }
-            if constexpr (KNOWN_ROW) {
-                // One row for the whole span: its A slice is loaded once.
-                if (nkb > 1 || !have_arow) {
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) {
-                        const int v = kb * PER_BLK + t * G + g.gl;
-                        if (v < nvec) load_elems<DTA, VECN>(a.A, r0 * a.lda + (int64_t)v * VECN, arow[t]);
-                        else
+            for (int u = 0; u < U; ++u) ok[u] = (eb + u >= e0) && (eb + u < e1);
+            // the lane that will store nonzero gl fetches its value now
+            float sv = 0.f;
+            const int64_t ew = eb + g.gl;
+            const bool writer = (g.gl < U) && (ew >= e0) && (ew < e1);
+            if (writer) {
+                sv = a.vals ? __ldg(a.vals + ew) : 1.f;
+                if (a.vals2) sv *= __ldg(a.vals2 + ew);
+            }
+
+            float p[U];
 #pragma unroll
-                            for (int q = 0; q < VECN; ++q) arow[t][q] = 0.f;
-                    }
-                    have_arow = true;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int t = 0; t < NV; ++t)
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) p[u] = fmaf(arow[t][q], bv[u][t][q], p[u]);
-            } else {
-                // A rows: loaded where the row changes inside the batch, issued
-                // together with the B gathers.
-                float av[U][NV][VECN];
+            for (int u = 0; u < U; ++u) p[u] = 0.f;
+            for (int kb = 0; kb < nkb; ++kb) {
+                Raw<DTB, VECN> bw[U][NV];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const bool fresh = (u == 0) || (row[u] != row[u > 0 ? u - 1 : 0]) || !ok[u > 0 ? u - 1 : 0];
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) {
-                        const int v = kb * PER_BLK + t * G + g.gl;
-                        if (fresh) {
-                            if (ok[u] && v < nvec) {
-                                load_elems<DTA, VECN>(a.A, (int64_t)row[u] * a.lda + (int64_t)v * VECN, av[u][t]);
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < VECN; ++q) av[u][t][q] = 0.f;
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < VECN; ++q) av[u][t][q] = av[u > 0 ? u - 1 : 0][t][q];
-                        }
+                    for (int t2 = 0; t2 < NV; ++t2) {
+                        const int v = kb * PER_BLK + t2 * G + g.gl;
+                        if (ok[u] && v < nvec) load_raw<DTB, VECN>(a.B, (int64_t)j[u] * a.ldb + (int64_t)v * VECN, bw[u][t2]);
+                        else zero_raw(bw[u][t2]);
                     }
                 }
 #pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (!ok[u]) continue;
+                    if (nkb > 1 || row[u] != ra) {
+                        // row change (rare inside a batch): reload the A slice
+#pragma unroll
+                        for (int t2 = 0; t2 < NV; ++t2) {
+                            const int v = kb * PER_BLK + t2 * G + g.gl;
+                            if (v < nvec) load_elems<DTA, VECN>(a.A, (int64_t)row[u] * a.lda + (int64_t)v * VECN, av[t2]);
+                            else
+#pragma unroll
+                                for (int q = 0; q < VECN; ++q) av[t2][q] = 0.f;
+                        }
+                        ra = (nkb == 1) ? row[u] : -1;
+                    }
+#pragma unroll
+                    for (int t2 = 0; t2 < NV; ++t2) {
+                        float bf[VECN];
+                        unpack_all<DTB, VECN>(bw[u][t2], bf);
+#pragma unroll
+                        for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t2][q], bf[q], p[u]);
+                    }
+                }
+            }
+
+            if constexpr (DTA == DT_E4M3) {
+#pragma unroll
                 for (int u = 0; u < U; ++u)
-#pragma unroll
-                    for (int t = 0; t < NV; ++t)
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[u][t][q], bv[u][t][q], p[u]);
+                    if (ok[u]) p[u] *= __ldg(a.a_scale + row[u]) * __ldg(a.b_scale + j[u]);
             }
-        }
 
-        if constexpr (DTA == DT_E4M3) {
+            // Reduce-scatter over the low log2(U) lane bits: after the stage with
+            // distance d, lanes with bit d set keep the upper half of the list.
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (ok[u]) p[u] *= __ldg(a.a_scale + row[u]) * __ldg(a.b_scale + j[u]);
-        }
-
-        // Reduce-scatter over the low log2(U) lane bits: after the stage with
-        // distance d, lanes with bit d set keep the upper half of the list.
+            for (int d = U / 2; d >= 1; d >>= 1) {
+                const bool upper = (g.gl & d) != 0;
 #pragma unroll
-        for (int d = U / 2; d >= 1; d >>= 1) {
-            const bool upper = (g.gl & d) != 0;
-#pragma unroll
-            for (int i = 0; i < d; ++i) {
-                const float send = upper ? p[i] : p[i + d];
-                const float keep = upper ? p[i + d] : p[i];
-                p[i] = keep + __shfl_xor_sync(g.mask, send, d, G);
+                for (int i = 0; i < d; ++i) {
+                    const float send = upper ? p[i] : p[i + d];
+                    const float keep = upper ? p[i + d] : p[i];
+                    p[i] = keep + __shfl_xor_sync(g.mask, send, d, G);
+                }
             }
-        }
-        // Combine the G/U lane subsets that each hold a partial of nonzero gl % U.
+            // Combine the G/U lane subsets that each hold a partial of nonzero gl % U.
 #pragma unroll
-        for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(g.mask, p[0], d, G);
+            for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(g.mask, p[0], d, G);
 
-        if (g.gl < U) {
-            const int64_t e = eb + g.gl;
-            if (e >= e0 && e < e1) {
-                float s = a.vals ? __ldg(a.vals + e) : 1.f;
-                if (a.vals2) s *= __ldg(a.vals2 + e);
-                __stcs(a.out + e, s * p[0]);
-            }
+            if (writer) __stcs(a.out + ew, sv * p[0]);
         }
+        __syncwarp(g.mask);
     }
+    cp_async_wait<0>();
+}
+
+// Shared-memory words per group: the ring pipeline on the vector path, index
+// tiles on the element path.
+template <int DTA, int DTB, int VECN, int G, int NV, int U>
+__host__ __device__ constexpr int sddmm_group_words()
+{
+    return VECN > 1 ? pipe_words(G, NV, U, NV * (VECN * dt_bytes(DTA) / 16)) : tile_words(G);
 }
 
 template <int DTA, int DTB, int VECN, int G, int NV, int U>
-__global__ void __launch_bounds__(256) k_sddmm(const SddmmArgs a)
+__global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_sddmm(const SddmmArgs a)
 {
+    extern __shared__ int smem[];
+    constexpr int WORDS = sddmm_group_words<DTA, DTB, VECN, G, NV, U>();
+    int* sm = smem + (threadIdx.x / G) * WORDS;
     const Group<G> g;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool pipe = (VECN > 1) && (a.K / VECN <= G * NV);     // one K block: ring pipeline
     if (a.bnd) {
         for (int64_t c = gid; c < a.nchunks; c += ngroups) {
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-            sddmm_span<DTA, DTB, VECN, G, NV, U, false>(a, g, b0.x, b0.y, b1.y);
+            if constexpr (VECN > 1) {
+                if (pipe) { sddmm_span_pipe<DTA, DTB, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y); continue; }
+            }
+            sddmm_span<DTA, DTB, VECN, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y);
         }
     } else {
         for (int64_t r = gid; r < a.M; r += ngroups) {
             const int64_t e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
-            sddmm_span<DTA, DTB, VECN, G, NV, U, true>(a, g, r, e0, e1);
+            if constexpr (VECN > 1) {
+                if (pipe) { sddmm_span_pipe<DTA, DTB, G, NV, U, true>(a, g, sm, r, e0, e1); continue; }
+            }
+            sddmm_span<DTA, DTB, VECN, G, NV, U, true>(a, g, sm, r, e0, e1);
         }
     }
 }
 
 // Kernel for (dtypes, vector mode, shape index).
 template <int DTA, int DTB, int VECN>
-inline const void* sddmm_kernel_for(int shape)
+inline const void* sddmm_kernel_for(int shape, int* words)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_) case i: return (const void*)&k_sddmm<DTA, DTB, VECN, G_, NV_, U_>;
+#define X(i, G_, NV_, U_)                                                       \
+    case i:                                                                     \
+        *words = sddmm_group_words<DTA, DTB, VECN, G_, NV_, U_>();              \
+        return (const void*)&k_sddmm<DTA, DTB, VECN, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -177,17 +197,24 @@ inline const void* sddmm_kernel_for(int shape)
 template <int DTA, int DTB>
 cudaError_t launch_sddmm_t(const Launch& L, const SddmmArgs& a, cudaStream_t s)
 {
-    const void* fn = L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape)
-                           : sddmm_kernel_for<DTA, DTB, 1>(L.shape);
+    int words = 0;
+    const void* fn = L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape, &words)
+                           : sddmm_kernel_for<DTA, DTB, 1>(L.shape, &words);
     if (!fn) return cudaErrorInvalidValue;
     const Shape sh = shape_at(L.shape);
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
-    const int64_t groups_per_cta = L.threads / sh.G;
+    int threads = L.threads;
+    while (threads > sh.G && threads > 32 && (size_t)(threads / sh.G) * words * sizeof(int) > kMaxSmemPerCta)
+        threads /= 2;                                   // a CTA must fit the per-CTA shared-memory limit
+    const int64_t groups_per_cta = threads / sh.G;
     int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    const size_t smem = (size_t)groups_per_cta * words * sizeof(int);
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(L.threads), args, 0, s);
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, s);
 }
 
 }  // namespace spk

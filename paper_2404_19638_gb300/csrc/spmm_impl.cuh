@@ -3,8 +3,9 @@
 // transposed pattern whose values are gathered through a permutation.
 //
 // A lane group of G lanes owns K-slices of one output row at a time and walks
-// a span of consecutive nonzeros U at a time: U broadcast index loads, U*NV
-// 16-byte gathers of B rows in flight per lane, FP32 FMAs into registers.
+// a span of consecutive nonzeros U at a time: the indices (and values) arrive
+// through shared memory one tile ahead (cp.async, see tiles.cuh); U*NV 16-byte
+// gathers of B rows are in flight per lane; FP32 FMAs into registers.
 // When the COO row changes, the finished row is stored; rows without
 // nonzeros between two stored rows are written as zeros.
 //
@@ -15,7 +16,7 @@
 // adds the pieces in chunk order and writes the row.  The sum order is fixed
 // by the schedule, so results are bitwise reproducible.
 #pragma once
-#include "common.cuh"
+#include "pipe.cuh"
 
 namespace spk {
 
@@ -124,10 +125,12 @@ __device__ __forceinline__ void finish_piece(const SpmmArgs& a, const Group<G>& 
 }
 
 template <int DTB, int VECN, int G, int NV, int U, bool KNOWN_ROW>
-__device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, int kb, int nkb,
+__device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, int* tiles, int kb, int nkb,
                                           int64_t r0, int64_t e0, int64_t r1, int64_t e1,
                                           const int4 meta, int head_s0)
 {
+    constexpr int T = TileCfg<G>::T;
+    static_assert(T % U == 0, "tile must hold whole batches");
     const int nvec = a.K / VECN;
     float acc[NV][VECN];
 #pragma unroll
@@ -145,67 +148,118 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
             write_row<VECN, G, NV>(a, g, kb, nvec, row, acc);
     };
 
-    for (int64_t eb = e0 & ~int64_t(U - 1); eb < e1; eb += U) {
-        int j[U], row[U];
-        float s[U];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t e = eb + u;
-            ok[u] = (e >= e0) && (e < e1);
-            j[u] = ok[u] ? __ldg(a.colidx + e) : 0;
-            if constexpr (KNOWN_ROW) row[u] = (int)r0;
-            else row[u] = ok[u] ? __ldg(a.rowidx + e) : 0;
-            const int64_t vi = a.vperm ? (ok[u] ? (int64_t)__ldg(a.vperm + e) : 0) : e;
-            float sv = 0.f;
-            if (ok[u]) {
-                sv = a.vals ? __ldg(a.vals + vi) : 1.f;
-                if (a.vals2) sv *= __ldg(a.vals2 + vi);
-                if constexpr (DTB == DT_E4M3) sv *= __ldg(a.b_scale + j[u]);
-            }
-            s[u] = sv;
-        }
-        float bv[U][NV][VECN];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-#pragma unroll
-            for (int t = 0; t < NV; ++t) {
-                const int v = kb * G * NV + t * G + g.gl;
-                if (ok[u] && v < nvec) {
-                    load_elems<DTB, VECN>(a.B, (int64_t)j[u] * a.ldb + (int64_t)v * VECN, bv[u][t]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < VECN; ++q) bv[u][t][q] = 0.f;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            if constexpr (!KNOWN_ROW) {
-                if (row[u] != cur) {
-                    flush(cur);
-                    for (int64_t rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
-                    cur = row[u];
-#pragma unroll
-                    for (int t = 0; t < NV; ++t)
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < NV; ++t)
-#pragma unroll
-                for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bv[u][t][q], acc[t][q]);
-        }
+    const int64_t tb0 = e0 & ~int64_t(3);
+    const int32_t* rsrc = KNOWN_ROW ? nullptr : a.rowidx;
+    const float* vsrc = a.vals_staged ? a.vals : nullptr;
+    if (e0 < e1) {
+        fill_tile<G>(tiles, 0, tb0, a.nnz, g.gl, a.colidx, rsrc, vsrc);
+        cp_async_commit();
     }
+    int t = 0;
+    for (int64_t tb = tb0; tb < e1; tb += T, ++t) {
+        const int buf = t & 1;
+        if (tb + T < e1) fill_tile<G>(tiles, buf ^ 1, tb + T, a.nnz, g.gl, a.colidx, rsrc, vsrc);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp(g.mask);
+        const int* colt = tiles + buf * T;
+        const int* rowt = tiles + 2 * T + buf * T;
+        const float* valt = reinterpret_cast<const float*>(tiles + 4 * T + buf * T);
+        for (int b = 0; b < T; b += U) {
+            const int64_t eb = tb + b;
+            if (eb >= e1) break;
+            int j[U], row[U];
+            float s[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; u += 4) {
+                const int4 c4 = *reinterpret_cast<const int4*>(colt + b + u);
+                j[u] = c4.x; j[u + 1] = c4.y; j[u + 2] = c4.z; j[u + 3] = c4.w;
+                if constexpr (KNOWN_ROW) {
+                    row[u] = row[u + 1] = row[u + 2] = row[u + 3] = (int)r0;
+                } else {
+                    const int4 r4 = *reinterpret_cast<const int4*>(rowt + b + u);
+                    row[u] = r4.x; row[u + 1] = r4.y; row[u + 2] = r4.z; row[u + 3] = r4.w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) ok[u] = (eb + u >= e0) && (eb + u < e1);
+            if (a.vals_staged) {
+#pragma unroll
+                for (int u = 0; u < U; u += 4) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(valt + b + u);
+                    s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    float sv = 1.f;
+                    if (ok[u]) {
+                        const int64_t e = eb + u;
+                        const int64_t vi = a.vperm ? (int64_t)__ldg(a.vperm + e) : e;
+                        if (a.vals) sv = __ldg(a.vals + vi);
+                        if (a.vals2) sv *= __ldg(a.vals2 + vi);
+                    }
+                    s[u] = sv;
+                }
+            }
+            if constexpr (DTB == DT_E4M3) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (ok[u]) s[u] *= __ldg(a.b_scale + j[u]);
+            }
+            Raw<DTB, VECN> bw[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int t2 = 0; t2 < NV; ++t2) {
+                    const int v = kb * G * NV + t2 * G + g.gl;
+                    if (ok[u] && v < nvec) load_raw<DTB, VECN>(a.B, (int64_t)j[u] * a.ldb + (int64_t)v * VECN, bw[u][t2]);
+                    else zero_raw(bw[u][t2]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                if constexpr (!KNOWN_ROW) {
+                    if (row[u] != cur) {
+                        flush(cur);
+                        for (int64_t rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
+                        cur = row[u];
+#pragma unroll
+                        for (int t2 = 0; t2 < NV; ++t2)
+#pragma unroll
+                            for (int q = 0; q < VECN; ++q) acc[t2][q] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int t2 = 0; t2 < NV; ++t2) {
+                    float bf[VECN];
+                    unpack_all<DTB, VECN>(bw[u][t2], bf);
+#pragma unroll
+                    for (int q = 0; q < VECN; ++q) acc[t2][q] = fmaf(s[u], bf[q], acc[t2][q]);
+                }
+            }
+        }
+        __syncwarp(g.mask);
+    }
+    cp_async_wait<0>();
     flush(cur);
     for (int64_t rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
 template <int DTB, int VECN, int G, int NV, int U>
-__global__ void __launch_bounds__(256) k_spmm(const SpmmArgs a)
+__host__ __device__ constexpr int spmm_group_words()
 {
+    return VECN > 1 ? pipe_words(G, NV, U, 0) : tile_words(G);
+}
+
+template <int DTB, int VECN, int G, int NV, int U>
+__global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_spmm(const SpmmArgs a)
+{
+    extern __shared__ int smem[];
+    constexpr int WORDS = spmm_group_words<DTB, VECN, G, NV, U>();
+    int* sm = smem + (threadIdx.x / G) * WORDS;
     const Group<G> g;
     const int kb = blockIdx.y, nkb = gridDim.y;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
@@ -216,22 +270,31 @@ __global__ void __launch_bounds__(256) k_spmm(const SpmmArgs a)
             const int4 m = a.meta[c];
             if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
             const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-            spmm_span<DTB, VECN, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+            if constexpr (VECN > 1)
+                spmm_span_pipe<DTB, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+            else
+                spmm_span<DTB, VECN, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
         }
     } else {
         for (int64_t r = gid; r < a.M; r += ngroups) {
             const int64_t e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
-            spmm_span<DTB, VECN, G, NV, U, true>(a, g, kb, nkb, r, e0, r, e1,
-                                                 make_int4(-1, -1, (int)r, 0), -1);
+            const int4 m = make_int4(-1, -1, (int)r, 0);
+            if constexpr (VECN > 1)
+                spmm_span_pipe<DTB, G, NV, U, true>(a, g, sm, kb, nkb, r, e0, r, e1, m, -1);
+            else
+                spmm_span<DTB, VECN, G, NV, U, true>(a, g, sm, kb, nkb, r, e0, r, e1, m, -1);
         }
     }
 }
 
 template <int DTB, int VECN>
-inline const void* spmm_kernel_for(int shape)
+inline const void* spmm_kernel_for(int shape, int* words)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm<DTB, VECN, G_, NV_, U_>;
+#define X(i, G_, NV_, U_)                                                       \
+    case i:                                                                     \
+        *words = spmm_group_words<DTB, VECN, G_, NV_, U_>();                    \
+        return (const void*)&k_spmm<DTB, VECN, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -241,7 +304,9 @@ inline const void* spmm_kernel_for(int shape)
 template <int DTB>
 cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
 {
-    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape) : spmm_kernel_for<DTB, 1>(L.shape);
+    int words = 0;
+    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape, &words)
+                           : spmm_kernel_for<DTB, 1>(L.shape, &words);
     if (!fn) return cudaErrorInvalidValue;
     const Shape sh = shape_at(L.shape);
     const int vecn = L.vec ? vec_elems(DTB) : 1;
@@ -249,12 +314,18 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     const int nkb = (nvec + sh.G * sh.NV - 1) / (sh.G * sh.NV);
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
-    const int64_t groups_per_cta = L.threads / sh.G;
+    int threads = L.threads;
+    while (threads > sh.G && threads > 32 && (size_t)(threads / sh.G) * words * sizeof(int) > kMaxSmemPerCta)
+        threads /= 2;                                   // a CTA must fit the per-CTA shared-memory limit
+    const int64_t groups_per_cta = threads / sh.G;
     int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
     if (nkb > 65535) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)groups_per_cta * words * sizeof(int);
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)nkb), dim3(L.threads), args, 0, s);
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)nkb), dim3(threads), args, smem, s);
 }
 
 }  // namespace spk

@@ -119,9 +119,7 @@ def test_batch_equals_per_matrix_launches(spk, dt):
     for S, A, B, out, op, p in keep:
         vecn = 4 if dt == torch.float32 else 8
         nvec = p.K // vecn
-        shape = {4: (4, 1, 4), 8: (8, 1, 8 if dt == torch.float32 else 4), 16: (16, 1, 4)}.get(nvec, (4, 1, 4))
-        if nvec <= 2:
-            shape = (4, 1, 4)
+        shape = (4, 1, 4) if nvec <= 4 else ((8, 1, 4) if nvec <= 8 else (16, 1, 4))
         tune = {"variant": 2, "group_lanes": shape[0], "vecs_per_lane": shape[1], "unroll": shape[2]}
         if op == 0:
             want = spk.sddmm(S, A, B, tune=tune)
