@@ -3,8 +3,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
-#include <mutex>
 #include <new>
 #include <string>
 
@@ -29,22 +27,6 @@ int shape_index(int G, int NV, int U)
 }
 
 Shape shape_at(int i) { return kShapes[i]; }
-
-cudaError_t ensure_smem(const void* fn, size_t bytes)
-{
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    static std::mutex mu;
-    static std::map<std::pair<const void*, int>, size_t> done;
-    std::lock_guard<std::mutex> lock(mu);
-    size_t& have = done[{fn, dev}];
-    if (have >= bytes) return cudaSuccess;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) have = bytes;
-    return e;
-}
 
 cudaError_t launch_sddmm(int dta, int dtb, const Launch& L, const SddmmArgs& a, cudaStream_t s)
 {
@@ -245,14 +227,19 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
+// Default lane-group shape for a row of nvec 16-byte vectors: 8 lanes per row
+// (one 128-byte line per warp-wide load per row) with up to 4 vectors per
+// lane, 4 nonzeros in flight per group.
 static void default_shape(int op, int nvec, int* G, int* NV, int* U)
 {
-    if (nvec <= 4) { *G = 4; *NV = 1; *U = 4; }
-    else if (nvec <= 8) { *G = 8; *NV = 1; *U = 8; }
-    else if (nvec <= 16) { *G = 16; *NV = 1; *U = (op == OP_SDDMM) ? 4 : 8; }
-    else if (nvec <= 32) { *G = 32; *NV = 1; *U = 8; }
-    else if (nvec <= 64) { *G = 32; *NV = 2; *U = 4; }
-    else { *G = 32; *NV = 4; *U = 4; }
+    (void)op;
+    *U = 4;
+    if (nvec <= 4) { *G = 4; *NV = 1; }
+    else if (nvec <= 8) { *G = 8; *NV = 1; }
+    else if (nvec <= 16) { *G = 8; *NV = 2; }
+    else if (nvec <= 32) { *G = 8; *NV = 4; }
+    else if (nvec <= 64) { *G = 32; *NV = 2; }
+    else { *G = 32; *NV = 4; }
 }
 
 static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, const spk_tune* t, Launch* L)

@@ -25,8 +25,8 @@ struct BatchDesc {
 };
 
 // (G, NV, U) shapes available to batched items; class = dtype * 8 + position
-// in this list.  Each (op, class) routine is a separate non-inlined function;
-// every warp owns a fixed shared-memory region big enough for any of them.
+// in this list.  Each (op, class) routine is a separate non-inlined function,
+// so the merged kernel needs no more registers than its largest routine.
 #define SPK_BATCH_SHAPES(X) \
     X(0, 4, 1, 4)           \
     X(1, 8, 1, 4)           \
@@ -39,30 +39,22 @@ static const Shape kBatchShapeList[kBatchShapes] = {
 #undef X
 };
 
-__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
-// Shared-memory words of one warp: the largest ring of any batched shape
-// (an SDDMM group also keeps A slices; one 16-byte vector per lane).
-constexpr int kWarpWords = cmax(cmax((32 / 4) * pipe_words(4, 1, 4, 1), (32 / 8) * pipe_words(8, 1, 4, 1)),
-                                (32 / 16) * pipe_words(16, 1, 4, 1));
-constexpr int kBatchThreads = 128;
-constexpr size_t kBatchSmem = (size_t)(kBatchThreads / 32) * kWarpWords * sizeof(int);
+constexpr int kBatchThreads = 256;
 
+// SDDMM: one chunk per warp (groups take interleaved batches of it).
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit, int* warp_sm)
+__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit)
 {
-    const Group<G> g;
-    int* sm = warp_sm + ((threadIdx.x & 31) / G) * pipe_words(G, NV, U, NV);
-    const int64_t c = unit * (32 / G) + ((threadIdx.x & 31) / G);
-    if (c >= a.nchunks) return;
-    const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-    sddmm_span_pipe<DT, DT, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y);
+    if (unit >= a.nchunks) return;
+    const int2 b0 = a.bnd[unit], b1 = a.bnd[unit + 1];
+    sddmm_warp_span<DT, DT, G, NV, U, false>(a, threadIdx.x & 31, b0.x, b0.y, b1.y);
 }
 
+// SpMM: one chunk per lane group, 32/G consecutive chunks per unit.
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb, int* warp_sm)
+__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb)
 {
     const Group<G> g;
-    int* sm = warp_sm + ((threadIdx.x & 31) / G) * pipe_words(G, NV, U, 0);
     const int kb = (int)(unit % nkb);
     const int64_t c = (unit / nkb) * (32 / G) + ((threadIdx.x & 31) / G);
     if (c >= a.nchunks) return;
@@ -70,15 +62,13 @@ __device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, in
     const int4 m = a.meta[c];
     if (b1.y == b0.y && m.z < b0.x) return;
     const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-    spmm_span_pipe<DT, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    spmm_group_span<DT, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
 }
 
 __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
                                                const int64_t* __restrict__ unit_begin, int64_t total_units,
                                                unsigned long long* counter, unsigned int* done)
 {
-    extern __shared__ int smem[];
-    int* warp_sm = smem + (threadIdx.x / 32) * kWarpWords;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long u = 0;
@@ -96,16 +86,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __rest
         if (d.op == 0) {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local, warp_sm); break;              \
-    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local, warp_sm); break;
+    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local); break;              \
+    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
         } else {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb, warp_sm); break;        \
-    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb, warp_sm); break;
+    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb); break;        \
+    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
@@ -223,7 +213,7 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
             a.B = it.B; a.ldb = it.ldb; a.b_scale = nullptr;
             a.out = reinterpret_cast<float*>(it.out);
             a.bnd = S->bnd; a.nchunks = S->nchunks;
-            P.unit_begin[m + 1] = units + (S->nnz > 0 ? wunits : 0);
+            P.unit_begin[m + 1] = units + (S->nnz > 0 ? S->nchunks : 0);     // one chunk per warp
         } else {
             d.nkb = (nvec + G * NV - 1) / (G * NV);
             SpmmArgs& a = d.sp;
@@ -288,8 +278,7 @@ extern "C" spk_status spk_batch_create(const spk_batch_item* items, int32_t coun
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = ensure_smem((const void*)k_batch, kBatchSmem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, kBatchSmem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, 0);
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
     spk_batch_s* B = new (std::nothrow) spk_batch_s();
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_create: out of host memory");
@@ -308,7 +297,7 @@ extern "C" spk_status spk_batch_run(spk_batch B, void* stream)
 {
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_run: handle is NULL");
     if (B->total_units == 0) return SPK_OK;
-    k_batch<<<B->grid, kBatchThreads, kBatchSmem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
+    k_batch<<<B->grid, kBatchThreads, 0, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
                                                         B->d_counter, B->d_done);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_run: ") + cudaGetErrorString(e));

@@ -293,9 +293,10 @@ struct Shape { int G, NV, U; };
     X(8, 32, 4, 4)    \
     X(9, 16, 1, 4)    \
     X(10, 8, 2, 4)    \
-    X(11, 8, 1, 4)
+    X(11, 8, 1, 4)    \
+    X(12, 8, 4, 4)
 
-constexpr int kNumShapes = 12;
+constexpr int kNumShapes = 13;
 int shape_index(int G, int NV, int U);   // -1 if not compiled
 Shape shape_at(int i);
 
@@ -349,13 +350,7 @@ cudaError_t launch_cast(const float* x, int64_t n, int dt, void* out, cudaStream
 cudaError_t launch_quant_e4m3(const float* X, int64_t M, int64_t K, int64_t ldx, uint8_t* Q, int64_t ldq,
                               float* scales, cudaStream_t s);
 
-constexpr size_t kMaxSmemPerCta = 227 * 1024;
-
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// Opt a kernel into `bytes` of dynamic shared memory (needed above 48 KB);
-// remembered per kernel and device.
-cudaError_t ensure_smem(const void* fn, size_t bytes);
 
 }  // namespace spk
 

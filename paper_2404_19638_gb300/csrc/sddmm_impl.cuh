@@ -17,7 +17,7 @@
 // long rows are cut into pieces; SDDMM outputs are per nonzero, so pieces
 // need no combining.
 #pragma once
-#include "pipe.cuh"
+#include "lean.cuh"
 
 namespace spk {
 
@@ -142,52 +142,65 @@ __device__ __forceinline__ void sddmm_span(const SddmmArgs& a, const Group<G>& g
     cp_async_wait<0>();
 }
 
-// Shared-memory words per group: the ring pipeline on the vector path, index
-// tiles on the element path.
+// Element path (operands not 16-byte aligned / K not a multiple of a vector):
+// one group per span, index tiles in shared memory.
 template <int DTA, int DTB, int VECN, int G, int NV, int U>
-__host__ __device__ constexpr int sddmm_group_words()
-{
-    return VECN > 1 ? pipe_words(G, NV, U, NV * (VECN * dt_bytes(DTA) / 16)) : tile_words(G);
-}
-
-template <int DTA, int DTB, int VECN, int G, int NV, int U>
-__global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_sddmm(const SddmmArgs a)
+__global__ void __launch_bounds__(256, min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_sddmm(const SddmmArgs a)
 {
     extern __shared__ int smem[];
-    constexpr int WORDS = sddmm_group_words<DTA, DTB, VECN, G, NV, U>();
-    int* sm = smem + (threadIdx.x / G) * WORDS;
+    int* sm = smem + (threadIdx.x / G) * tile_words(G);
     const Group<G> g;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const bool pipe = (VECN > 1) && (a.K / VECN <= G * NV);     // one K block: ring pipeline
     if (a.bnd) {
         for (int64_t c = gid; c < a.nchunks; c += ngroups) {
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-            if constexpr (VECN > 1) {
-                if (pipe) { sddmm_span_pipe<DTA, DTB, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y); continue; }
-            }
             sddmm_span<DTA, DTB, VECN, G, NV, U, false>(a, g, sm, b0.x, b0.y, b1.y);
         }
     } else {
         for (int64_t r = gid; r < a.M; r += ngroups) {
             const int64_t e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
-            if constexpr (VECN > 1) {
-                if (pipe) { sddmm_span_pipe<DTA, DTB, G, NV, U, true>(a, g, sm, r, e0, e1); continue; }
-            }
             sddmm_span<DTA, DTB, VECN, G, NV, U, true>(a, g, sm, r, e0, e1);
         }
     }
 }
 
-// Kernel for (dtypes, vector mode, shape index).
+// Vector path: one warp per span (a chunk of the balanced schedule, or a row).
+template <int DTA, int DTB, int G, int NV, int U>
+__global__ void __launch_bounds__(256, min_ctas(U * NV * 4)) k_sddmm_lean(const SddmmArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    if (a.bnd) {
+        for (int64_t c = wid; c < a.nchunks; c += nwarps) {
+            const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+            sddmm_warp_span<DTA, DTB, G, NV, U, false>(a, lane, b0.x, b0.y, b1.y);
+        }
+    } else {
+        for (int64_t r = wid; r < a.M; r += nwarps) {
+            const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
+            sddmm_warp_span<DTA, DTB, G, NV, U, true>(a, lane, (int)r, e0, e1);
+        }
+    }
+}
+
 template <int DTA, int DTB, int VECN>
-inline const void* sddmm_kernel_for(int shape, int* words)
+inline const void* sddmm_kernel_for(int shape)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_)                                                       \
-    case i:                                                                     \
-        *words = sddmm_group_words<DTA, DTB, VECN, G_, NV_, U_>();              \
-        return (const void*)&k_sddmm<DTA, DTB, VECN, G_, NV_, U_>;
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_sddmm<DTA, DTB, VECN, G_, NV_, U_>;
+        SPK_SHAPES(X)
+#undef X
+    }
+    return nullptr;
+}
+
+template <int DTA, int DTB>
+inline const void* sddmm_lean_kernel_for(int shape)
+{
+    switch (shape) {
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_sddmm_lean<DTA, DTB, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -197,24 +210,20 @@ inline const void* sddmm_kernel_for(int shape, int* words)
 template <int DTA, int DTB>
 cudaError_t launch_sddmm_t(const Launch& L, const SddmmArgs& a, cudaStream_t s)
 {
-    int words = 0;
-    const void* fn = L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape, &words)
-                           : sddmm_kernel_for<DTA, DTB, 1>(L.shape, &words);
-    if (!fn) return cudaErrorInvalidValue;
     const Shape sh = shape_at(L.shape);
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
-    int threads = L.threads;
-    while (threads > sh.G && threads > 32 && (size_t)(threads / sh.G) * words * sizeof(int) > kMaxSmemPerCta)
-        threads /= 2;                                   // a CTA must fit the per-CTA shared-memory limit
-    const int64_t groups_per_cta = threads / sh.G;
-    int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
+    const bool lean = L.vec && (a.K / vec_elems(DTB)) <= sh.G * sh.NV;
+    const void* fn = lean ? sddmm_lean_kernel_for<DTA, DTB>(L.shape)
+                          : (L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape)
+                                   : sddmm_kernel_for<DTA, DTB, 1>(L.shape));
+    if (!fn) return cudaErrorInvalidValue;
+    const int64_t per_cta = lean ? L.threads / 32 : L.threads / sh.G;     // spans per CTA
+    int64_t blocks = (items + per_cta - 1) / per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    const size_t smem = (size_t)groups_per_cta * words * sizeof(int);
-    cudaError_t e = ensure_smem(fn, smem);
-    if (e != cudaSuccess) return e;
+    const size_t smem = lean ? 0 : (size_t)(L.threads / sh.G) * tile_words(sh.G) * sizeof(int);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(threads), args, smem, s);
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(L.threads), args, smem, s);
 }
 
 }  // namespace spk

@@ -16,7 +16,7 @@
 // adds the pieces in chunk order and writes the row.  The sum order is fixed
 // by the schedule, so results are bitwise reproducible.
 #pragma once
-#include "pipe.cuh"
+#include "lean.cuh"
 
 namespace spk {
 
@@ -248,22 +248,19 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
     for (int64_t rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
+// One group per span (a chunk of the balanced schedule, or a row).  The
+// vector path runs the lean span without shared memory; the element path
+// streams index tiles through shared memory.
 template <int DTB, int VECN, int G, int NV, int U>
-__host__ __device__ constexpr int spmm_group_words()
-{
-    return VECN > 1 ? pipe_words(G, NV, U, 0) : tile_words(G);
-}
-
-template <int DTB, int VECN, int G, int NV, int U>
-__global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_spmm(const SpmmArgs a)
+__global__ void __launch_bounds__(256, VECN > 1 ? min_ctas(U * NV * 4) : min_ctas(U * NV * Raw<DTB, VECN>::NW))
+    k_spmm(const SpmmArgs a)
 {
     extern __shared__ int smem[];
-    constexpr int WORDS = spmm_group_words<DTB, VECN, G, NV, U>();
-    int* sm = smem + (threadIdx.x / G) * WORDS;
     const Group<G> g;
     const int kb = blockIdx.y, nkb = gridDim.y;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    int* sm = smem + (threadIdx.x / G) * tile_words(G);
     if (a.bnd) {
         for (int64_t c = gid; c < a.nchunks; c += ngroups) {
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
@@ -271,16 +268,16 @@ __global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB,
             if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
             const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
             if constexpr (VECN > 1)
-                spmm_span_pipe<DTB, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+                spmm_group_span<DTB, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
             else
                 spmm_span<DTB, VECN, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
         }
     } else {
         for (int64_t r = gid; r < a.M; r += ngroups) {
-            const int64_t e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
+            const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
             const int4 m = make_int4(-1, -1, (int)r, 0);
             if constexpr (VECN > 1)
-                spmm_span_pipe<DTB, G, NV, U, true>(a, g, sm, kb, nkb, r, e0, r, e1, m, -1);
+                spmm_group_span<DTB, G, NV, U, true>(a, g, kb, nkb, (int)r, e0, (int)r, e1, m, -1);
             else
                 spmm_span<DTB, VECN, G, NV, U, true>(a, g, sm, kb, nkb, r, e0, r, e1, m, -1);
         }
@@ -288,13 +285,10 @@ __global__ void __launch_bounds__(256, VECN > 1 ? 2 : min_ctas(U * NV * Raw<DTB,
 }
 
 template <int DTB, int VECN>
-inline const void* spmm_kernel_for(int shape, int* words)
+inline const void* spmm_kernel_for(int shape)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_)                                                       \
-    case i:                                                                     \
-        *words = spmm_group_words<DTB, VECN, G_, NV_, U_>();                    \
-        return (const void*)&k_spmm<DTB, VECN, G_, NV_, U_>;
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm<DTB, VECN, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -304,9 +298,7 @@ inline const void* spmm_kernel_for(int shape, int* words)
 template <int DTB>
 cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
 {
-    int words = 0;
-    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape, &words)
-                           : spmm_kernel_for<DTB, 1>(L.shape, &words);
+    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape) : spmm_kernel_for<DTB, 1>(L.shape);
     if (!fn) return cudaErrorInvalidValue;
     const Shape sh = shape_at(L.shape);
     const int vecn = L.vec ? vec_elems(DTB) : 1;
@@ -314,18 +306,13 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     const int nkb = (nvec + sh.G * sh.NV - 1) / (sh.G * sh.NV);
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
-    int threads = L.threads;
-    while (threads > sh.G && threads > 32 && (size_t)(threads / sh.G) * words * sizeof(int) > kMaxSmemPerCta)
-        threads /= 2;                                   // a CTA must fit the per-CTA shared-memory limit
-    const int64_t groups_per_cta = threads / sh.G;
+    const int64_t groups_per_cta = L.threads / sh.G;
     int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
     if (nkb > 65535) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)groups_per_cta * words * sizeof(int);
-    cudaError_t e = ensure_smem(fn, smem);
-    if (e != cudaSuccess) return e;
+    const size_t smem = L.vec ? 0 : (size_t)groups_per_cta * tile_words(sh.G) * sizeof(int);
     void* args[] = {(void*)&a};
-    return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)nkb), dim3(threads), args, smem, s);
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)nkb), dim3(L.threads), args, smem, s);
 }
 
 }  // namespace spk

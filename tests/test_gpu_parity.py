@@ -31,7 +31,7 @@ def _case(M, N, K, seed, long_row=0, dtype=np.float32):
     return rp, ci, vals, A, B
 
 
-SHAPES = [(4, 1, 4), (8, 1, 8), (16, 1, 8), (32, 1, 8), (8, 2, 8), (16, 2, 8), (32, 2, 4), (4, 2, 4), (32, 4, 4),
+SHAPES = [(4, 1, 4), (8, 1, 8), (16, 1, 8), (32, 1, 8), (8, 2, 8), (16, 2, 8), (32, 2, 4), (4, 2, 4), (32, 4, 4), (8, 4, 4),
           (16, 1, 4), (8, 2, 4), (8, 1, 4)]
 
 
