@@ -50,19 +50,20 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
 
     float av[NV][VECN];
     int cur = -1;
-    for (int wb = e0 & ~3; wb < e1; wb += WB) {
-        const int eg = wb + grp * U;
-        if (eg >= e1) continue;
-        const bool full = (eg >= e0) && (eg + U <= e1);
-        int j[U], row[U];
-        if (full) {
+    // Indices of the next batch are loaded while the current batch's rows are
+    // being gathered, so a batch costs one memory round trip, not two.
+    int nj[U], nrow[U];
+    bool nfull = false;
+    auto load_idx = [&](int eg) {
+        nfull = (eg >= e0) && (eg + U <= e1);
+        if (nfull) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eg + u);
-                j[u] = c.x; j[u + 1] = c.y; j[u + 2] = c.z; j[u + 3] = c.w;
+                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eg + u);
-                    row[u] = r.x; row[u + 1] = r.y; row[u + 2] = r.z; row[u + 3] = r.w;
+                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
                 }
             }
         } else {
@@ -70,14 +71,24 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
             for (int u = 0; u < U; ++u) {
                 const int e = eg + u;
                 const bool ok = (e >= e0) && (e < e1);
-                j[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) row[u] = ok ? __ldg(a.rowidx + e) : -1;
+                nj[u] = ok ? __ldg(a.colidx + e) : -1;
+                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
             }
         }
         if constexpr (KNOWN_ROW) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) row[u] = r0;
+            for (int u = 0; u < U; ++u) nrow[u] = r0;
         }
+    };
+    const int wb0 = e0 & ~3;
+    if (wb0 + grp * U < e1) load_idx(wb0 + grp * U);
+    for (int wb = wb0; wb < e1; wb += WB) {
+        const int eg = wb + grp * U;
+        if (eg >= e1) continue;
+        const bool full = nfull;
+        int j[U], row[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; }
         // the lane that stores nonzero eg + gl fetches its scale early
         const int ew = eg + gl;
         const bool writer = (gl < U) && (ew >= e0) && (ew < e1);
@@ -98,6 +109,7 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
                     zero_raw(bw[u][t]);
             }
         }
+        if (eg + WB < e1) load_idx(eg + WB);
         float p[U];
         if (full && row[0] == cur && row[U - 1] == cur) {
 #pragma unroll
@@ -203,18 +215,21 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             write_row<VECN, G, NV>(a, g, kb, nvec, row, acc);
     };
 
-    for (int eb = e0 & ~3; eb < e1; eb += U) {
-        const bool full = (eb >= e0) && (eb + U <= e1);
-        int j[U], row[U];
-        float s[U];
-        if (full) {
+    // Indices and values of the next batch are loaded while the current
+    // batch's rows are being gathered (one memory round trip per batch).
+    int nj[U], nrow[U];
+    float ns[U];
+    bool nfull = false;
+    auto load_idx = [&](int eb) {
+        nfull = (eb >= e0) && (eb + U <= e1);
+        if (nfull) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eb + u);
-                j[u] = c.x; j[u + 1] = c.y; j[u + 2] = c.z; j[u + 3] = c.w;
+                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eb + u);
-                    row[u] = r.x; row[u + 1] = r.y; row[u + 2] = r.z; row[u + 3] = r.w;
+                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
                 }
             }
         } else {
@@ -222,33 +237,41 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             for (int u = 0; u < U; ++u) {
                 const int e = eb + u;
                 const bool ok = (e >= e0) && (e < e1);
-                j[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) row[u] = ok ? __ldg(a.rowidx + e) : -1;
+                nj[u] = ok ? __ldg(a.colidx + e) : -1;
+                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
             }
         }
         if constexpr (KNOWN_ROW) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) row[u] = r0;
+            for (int u = 0; u < U; ++u) nrow[u] = r0;
         }
-        if (full && vec_vals) {
+        if (nfull && vec_vals) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
-                s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
+                ns[u] = v4.x; ns[u + 1] = v4.y; ns[u + 2] = v4.z; ns[u + 3] = v4.w;
             }
         } else {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float sv = 0.f;
-                if (full || j[u] >= 0) {
+                if (nfull || nj[u] >= 0) {
                     const int e = eb + u;
                     const int vi = a.vperm ? __ldg(a.vperm + e) : e;
                     sv = a.vals ? __ldg(a.vals + vi) : 1.f;
                     if (a.vals2) sv *= __ldg(a.vals2 + vi);
                 }
-                s[u] = sv;
+                ns[u] = sv;
             }
         }
+    };
+    if (e0 < e1) load_idx(e0 & ~3);
+    for (int eb = e0 & ~3; eb < e1; eb += U) {
+        const bool full = nfull;
+        int j[U], row[U];
+        float s[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; s[u] = ns[u]; }
         if constexpr (DTB == DT_E4M3) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
@@ -266,6 +289,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
                     zero_raw(bw[u][t]);
             }
         }
+        if (eb + U < e1) load_idx(eb + U);
         if (full && (KNOWN_ROW || row[U - 1] == cur)) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
