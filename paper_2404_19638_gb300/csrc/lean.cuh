@@ -265,8 +265,10 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             }
         }
     };
+    // An empty span (e0 == e1) still rounds down to a batch start below e1:
+    // it must not enter the loop, whose indices come from load_idx.
     if (e0 < e1) load_idx(e0 & ~3);
-    for (int eb = e0 & ~3; eb < e1; eb += U) {
+    for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
         const bool full = nfull;
         int j[U], row[U];
         float s[U];
