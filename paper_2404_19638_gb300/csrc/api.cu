@@ -227,9 +227,6 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
-// L1 prefetch of the next batch's rows: on by default (1) or off (-1).
-static const int kDefaultPrefetch = 1;
-
 // Default lane-group shape for a row of nvec 16-byte vectors: 8 lanes per row
 // (one 128-byte line per warp-wide load per row) with up to 4 vectors per
 // lane, 4 nonzeros in flight per group.
@@ -262,13 +259,10 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
             G, NV, U);
     const int threads = (t && t->cta_threads) ? t->cta_threads : 256;
     REQUIRE(threads == 128 || threads == 256, SPK_ERR_ARG, "tune.cta_threads must be 128 or 256");
-    const int pf = (t && t->prefetch) ? t->prefetch : kDefaultPrefetch;
-    REQUIRE(pf == 1 || pf == -1, SPK_ERR_ARG, "tune.prefetch must be 0, 1 or -1");
     L->shape = idx;
     L->vec = vec;
     L->threads = threads;
     L->chunks = (variant == 2);
-    L->pf = (pf == 1);
     return SPK_OK;
 }
 
@@ -287,7 +281,6 @@ extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int3
     out->vecs_per_lane = sh.NV;
     out->unroll = sh.U;
     out->cta_threads = L.threads;
-    out->prefetch = L.pf ? 1 : -1;
     return SPK_OK;
 }
 

@@ -47,7 +47,7 @@ __device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit)
 {
     if (unit >= a.nchunks) return;
     const int2 b0 = a.bnd[unit], b1 = a.bnd[unit + 1];
-    sddmm_warp_span<DT, DT, G, NV, U, false, true>(a, threadIdx.x & 31, b0.x, b0.y, b1.y);
+    sddmm_warp_span<DT, DT, G, NV, U, false>(a, threadIdx.x & 31, b0.x, b0.y, b1.y);
 }
 
 // SpMM: one chunk per lane group, 32/G consecutive chunks per unit.
@@ -62,7 +62,7 @@ __device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, in
     const int4 m = a.meta[c];
     if (b1.y == b0.y && m.z < b0.x) return;
     const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-    spmm_group_span<DT, G, NV, U, false, true>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    spmm_group_span<DT, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
 }
 
 __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __restrict__ descs, int32_t count,

@@ -305,7 +305,6 @@ struct Launch {
     bool vec;          // 16-byte vector mode (else one element per lane slot)
     int threads;
     bool chunks;       // balanced schedule
-    bool pf;           // prefetch the next batch's rows into L1 (vector path)
 };
 
 // Launchers (one per dtype family; defined in the sddmm_*.cu / spmm_*.cu files).

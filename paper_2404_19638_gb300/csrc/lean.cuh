@@ -22,18 +22,6 @@ __device__ __forceinline__ unsigned group_mask(int lane)
     return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// Bring the 128-byte lines of a gathered row [row, row + bytes) into L1: lane
-// gl of the group fetches line gl (rows up to G lines long).  No registers
-// are tied up while the lines are in flight.
-template <int G>
-__device__ __forceinline__ void prefetch_row_l1(const char* row, unsigned bytes, int gl)
-{
-    const uintptr_t start = reinterpret_cast<uintptr_t>(row) & ~uintptr_t(127);
-    const uintptr_t end = reinterpret_cast<uintptr_t>(row) + bytes;
-    const uintptr_t line = start + (uintptr_t)gl * 128u;
-    if (line < end) asm volatile("prefetch.global.L1 [%0];" ::"l"(line));
-}
-
 // Four consecutive int32 (or float) entries at a 16-byte aligned position.
 __device__ __forceinline__ int4 ld4(const int32_t* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
 
@@ -42,7 +30,7 @@ __device__ __forceinline__ int4 ld4(const int32_t* p) { return __ldg(reinterpret
 // of the warp takes nonzeros [wb + kU, wb + kU + U).  Outputs are per nonzero,
 // so the groups never combine results.
 // ----------------------------------------------------------------------------
-template <int DTA, int DTB, int G, int NV, int U, bool KNOWN_ROW, bool PF = false>
+template <int DTA, int DTB, int G, int NV, int U, bool KNOWN_ROW>
 __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, int r0, int e0, int e1)
 {
     constexpr int VECN = vec_elems(DTB);
@@ -62,21 +50,20 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
 
     float av[NV][VECN];
     int cur = -1;
-    // Indices run ahead of the gathers: with PF, two batches ahead, and the
-    // rows of the next batch are prefetched into L1 one batch ahead, so a
-    // batch's own loads mostly hit L1; without PF, one batch ahead, so a
-    // batch costs one memory round trip, not two.
-    struct Idx { int j[U], row[U]; bool full; };
-    auto load_idx = [&](Idx& x, int eg) {
-        x.full = (eg >= e0) && (eg + U <= e1);
-        if (x.full) {
+    // Indices of the next batch are loaded while the current batch's rows are
+    // being gathered, so a batch costs one memory round trip, not two.
+    int nj[U], nrow[U];
+    bool nfull = false;
+    auto load_idx = [&](int eg) {
+        nfull = (eg >= e0) && (eg + U <= e1);
+        if (nfull) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eg + u);
-                x.j[u] = c.x; x.j[u + 1] = c.y; x.j[u + 2] = c.z; x.j[u + 3] = c.w;
+                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eg + u);
-                    x.row[u] = r.x; x.row[u + 1] = r.y; x.row[u + 2] = r.z; x.row[u + 3] = r.w;
+                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
                 }
             }
         } else {
@@ -84,36 +71,24 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
             for (int u = 0; u < U; ++u) {
                 const int e = eg + u;
                 const bool ok = (e >= e0) && (e < e1);
-                x.j[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) x.row[u] = ok ? __ldg(a.rowidx + e) : -1;
+                nj[u] = ok ? __ldg(a.colidx + e) : -1;
+                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
             }
         }
         if constexpr (KNOWN_ROW) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) x.row[u] = r0;
+            for (int u = 0; u < U; ++u) nrow[u] = r0;
         }
     };
-    const unsigned brow_bytes = (unsigned)a.K * dt_bytes(DTB);
-    auto prefetch = [&](const Idx& x) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (x.full || x.j[u] >= 0) prefetch_row_l1<G>(Bb + (size_t)(unsigned)x.j[u] * ldb_bytes, brow_bytes, gl);
-    };
-    Idx c0, c1, c2;
     const int wb0 = e0 & ~3;
-    if (wb0 + grp * U < e1) load_idx(c0, wb0 + grp * U);
-    if (PF && wb0 + grp * U + WB < e1) load_idx(c1, wb0 + grp * U + WB);
+    if (wb0 + grp * U < e1) load_idx(wb0 + grp * U);
     for (int wb = wb0; wb < e1; wb += WB) {
         const int eg = wb + grp * U;
         if (eg >= e1) continue;
-        if constexpr (PF) {
-            if (eg + WB < e1) prefetch(c1);
-            if (eg + 2 * WB < e1) load_idx(c2, eg + 2 * WB);
-        }
-        const bool full = c0.full;
+        const bool full = nfull;
         int j[U], row[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) { j[u] = c0.j[u]; row[u] = c0.row[u]; }
+        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; }
         // the lane that stores nonzero eg + gl fetches its scale early
         const int ew = eg + gl;
         const bool writer = (gl < U) && (ew >= e0) && (ew < e1);
@@ -134,12 +109,7 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
                     zero_raw(bw[u][t]);
             }
         }
-        if constexpr (PF) {
-            c0 = c1;
-            c1 = c2;
-        } else {
-            if (eg + WB < e1) load_idx(c0, eg + WB);
-        }
+        if (eg + WB < e1) load_idx(eg + WB);
         float p[U];
         if (full && row[0] == cur && row[U - 1] == cur) {
 #pragma unroll
@@ -214,7 +184,7 @@ template <int VECN, int G, int NV>
 __device__ __forceinline__ void finish_piece(const SpmmArgs& a, const Group<G>& g, int kb, int nkb, int nvec,
                                              int slot, int s0, int64_t row, const float (&acc)[NV][VECN]);
 
-template <int DTB, int G, int NV, int U, bool KNOWN_ROW, bool PF = false>
+template <int DTB, int G, int NV, int U, bool KNOWN_ROW>
 __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G>& g, int kb, int nkb, int r0,
                                                 int e0, int r1, int e1, const int4 meta, int head_s0)
 {
@@ -245,18 +215,21 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             write_row<VECN, G, NV>(a, g, kb, nvec, row, acc);
     };
 
-    // Indices and values run ahead of the gathers (see sddmm_warp_span).
-    struct Idx { int j[U], row[U]; float s[U]; bool full; };
-    auto load_idx = [&](Idx& x, int eb) {
-        x.full = (eb >= e0) && (eb + U <= e1);
-        if (x.full) {
+    // Indices and values of the next batch are loaded while the current
+    // batch's rows are being gathered (one memory round trip per batch).
+    int nj[U], nrow[U];
+    float ns[U];
+    bool nfull = false;
+    auto load_idx = [&](int eb) {
+        nfull = (eb >= e0) && (eb + U <= e1);
+        if (nfull) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eb + u);
-                x.j[u] = c.x; x.j[u + 1] = c.y; x.j[u + 2] = c.z; x.j[u + 3] = c.w;
+                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eb + u);
-                    x.row[u] = r.x; x.row[u + 1] = r.y; x.row[u + 2] = r.z; x.row[u + 3] = r.w;
+                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
                 }
             }
         } else {
@@ -264,55 +237,43 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             for (int u = 0; u < U; ++u) {
                 const int e = eb + u;
                 const bool ok = (e >= e0) && (e < e1);
-                x.j[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) x.row[u] = ok ? __ldg(a.rowidx + e) : -1;
+                nj[u] = ok ? __ldg(a.colidx + e) : -1;
+                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
             }
         }
         if constexpr (KNOWN_ROW) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) x.row[u] = r0;
+            for (int u = 0; u < U; ++u) nrow[u] = r0;
         }
-        if (x.full && vec_vals) {
+        if (nfull && vec_vals) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
-                x.s[u] = v4.x; x.s[u + 1] = v4.y; x.s[u + 2] = v4.z; x.s[u + 3] = v4.w;
+                ns[u] = v4.x; ns[u + 1] = v4.y; ns[u + 2] = v4.z; ns[u + 3] = v4.w;
             }
         } else {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float sv = 0.f;
-                if (x.full || x.j[u] >= 0) {
+                if (nfull || nj[u] >= 0) {
                     const int e = eb + u;
                     const int vi = a.vperm ? __ldg(a.vperm + e) : e;
                     sv = a.vals ? __ldg(a.vals + vi) : 1.f;
                     if (a.vals2) sv *= __ldg(a.vals2 + vi);
                 }
-                x.s[u] = sv;
+                ns[u] = sv;
             }
         }
     };
-    const unsigned brow_bytes = (unsigned)a.K * dt_bytes(DTB);
-    auto prefetch = [&](const Idx& x) {
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (x.full || x.j[u] >= 0) prefetch_row_l1<G>(Bb + (size_t)(unsigned)x.j[u] * ldb_bytes, brow_bytes, gl);
-    };
     // An empty span (e0 == e1) still rounds down to a batch start below e1:
     // it must not enter the loop, whose indices come from load_idx.
-    Idx c0, c1, c2;
-    if (e0 < e1) load_idx(c0, e0 & ~3);
-    if (PF && e0 < e1 && (e0 & ~3) + U < e1) load_idx(c1, (e0 & ~3) + U);
+    if (e0 < e1) load_idx(e0 & ~3);
     for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
-        if constexpr (PF) {
-            if (eb + U < e1) prefetch(c1);
-            if (eb + 2 * U < e1) load_idx(c2, eb + 2 * U);
-        }
-        const bool full = c0.full;
+        const bool full = nfull;
         int j[U], row[U];
         float s[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) { j[u] = c0.j[u]; row[u] = c0.row[u]; s[u] = c0.s[u]; }
+        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; s[u] = ns[u]; }
         if constexpr (DTB == DT_E4M3) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
@@ -330,12 +291,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
                     zero_raw(bw[u][t]);
             }
         }
-        if constexpr (PF) {
-            c0 = c1;
-            c1 = c2;
-        } else {
-            if (eb + U < e1) load_idx(c0, eb + U);
-        }
+        if (eb + U < e1) load_idx(eb + U);
         if (full && (KNOWN_ROW || row[U - 1] == cur)) {
 #pragma unroll
             for (int u = 0; u < U; ++u)

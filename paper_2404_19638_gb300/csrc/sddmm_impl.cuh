@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256, min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_
 }
 
 // Vector path: one warp per span (a chunk of the balanced schedule, or a row).
-template <int DTA, int DTB, int G, int NV, int U, bool PF>
+template <int DTA, int DTB, int G, int NV, int U>
 __global__ void __launch_bounds__(256, 3) k_sddmm_lean(const SddmmArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -175,12 +175,12 @@ __global__ void __launch_bounds__(256, 3) k_sddmm_lean(const SddmmArgs a)
     if (a.bnd) {
         for (int64_t c = wid; c < a.nchunks; c += nwarps) {
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-            sddmm_warp_span<DTA, DTB, G, NV, U, false, PF>(a, lane, b0.x, b0.y, b1.y);
+            sddmm_warp_span<DTA, DTB, G, NV, U, false>(a, lane, b0.x, b0.y, b1.y);
         }
     } else {
         for (int64_t r = wid; r < a.M; r += nwarps) {
             const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
-            sddmm_warp_span<DTA, DTB, G, NV, U, true, PF>(a, lane, (int)r, e0, e1);
+            sddmm_warp_span<DTA, DTB, G, NV, U, true>(a, lane, (int)r, e0, e1);
         }
     }
 }
@@ -197,12 +197,10 @@ inline const void* sddmm_kernel_for(int shape)
 }
 
 template <int DTA, int DTB>
-inline const void* sddmm_lean_kernel_for(int shape, bool pf)
+inline const void* sddmm_lean_kernel_for(int shape)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_)                                                              \
-    case i: return pf ? (const void*)&k_sddmm_lean<DTA, DTB, G_, NV_, U_, true>        \
-                      : (const void*)&k_sddmm_lean<DTA, DTB, G_, NV_, U_, false>;
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_sddmm_lean<DTA, DTB, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -216,7 +214,7 @@ cudaError_t launch_sddmm_t(const Launch& L, const SddmmArgs& a, cudaStream_t s)
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
     const bool lean = L.vec && (a.K / vec_elems(DTB)) <= sh.G * sh.NV;
-    const void* fn = lean ? sddmm_lean_kernel_for<DTA, DTB>(L.shape, L.pf)
+    const void* fn = lean ? sddmm_lean_kernel_for<DTA, DTB>(L.shape)
                           : (L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape)
                                    : sddmm_kernel_for<DTA, DTB, 1>(L.shape));
     if (!fn) return cudaErrorInvalidValue;

@@ -251,7 +251,7 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
 // One group per span (a chunk of the balanced schedule, or a row).  The
 // vector path runs the lean span without shared memory; the element path
 // streams index tiles through shared memory.
-template <int DTB, int VECN, int G, int NV, int U, bool PF>
+template <int DTB, int VECN, int G, int NV, int U>
 __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 3 : 2) : min_ctas(U * NV * Raw<DTB, VECN>::NW))
     k_spmm(const SpmmArgs a)
 {
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 3 : 2) : min_ct
             if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
             const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
             if constexpr (VECN > 1)
-                spmm_group_span<DTB, G, NV, U, false, PF>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+                spmm_group_span<DTB, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
             else
                 spmm_span<DTB, VECN, G, NV, U, false>(a, g, sm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
         }
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 3 : 2) : min_ct
             const int e0 = __ldg(a.rowptr + r), e1 = __ldg(a.rowptr + r + 1);
             const int4 m = make_int4(-1, -1, (int)r, 0);
             if constexpr (VECN > 1)
-                spmm_group_span<DTB, G, NV, U, true, PF>(a, g, kb, nkb, (int)r, e0, (int)r, e1, m, -1);
+                spmm_group_span<DTB, G, NV, U, true>(a, g, kb, nkb, (int)r, e0, (int)r, e1, m, -1);
             else
                 spmm_span<DTB, VECN, G, NV, U, true>(a, g, sm, kb, nkb, r, e0, r, e1, m, -1);
         }
@@ -285,12 +285,10 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 3 : 2) : min_ct
 }
 
 template <int DTB, int VECN>
-inline const void* spmm_kernel_for(int shape, bool pf)
+inline const void* spmm_kernel_for(int shape)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_)                                                              \
-    case i: return (pf && VECN > 1) ? (const void*)&k_spmm<DTB, VECN, G_, NV_, U_, true> \
-                                    : (const void*)&k_spmm<DTB, VECN, G_, NV_, U_, false>;
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm<DTB, VECN, G_, NV_, U_>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -300,7 +298,7 @@ inline const void* spmm_kernel_for(int shape, bool pf)
 template <int DTB>
 cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
 {
-    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape, L.pf) : spmm_kernel_for<DTB, 1>(L.shape, false);
+    const void* fn = L.vec ? spmm_kernel_for<DTB, vec_elems(DTB)>(L.shape) : spmm_kernel_for<DTB, 1>(L.shape);
     if (!fn) return cudaErrorInvalidValue;
     const Shape sh = shape_at(L.shape);
     const int vecn = L.vec ? vec_elems(DTB) : 1;
