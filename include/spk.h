@@ -73,9 +73,8 @@ typedef struct spk_tune {
     int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
     int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
     int32_t cta_threads;    /* threads per CTA: 128, 256                           */
-    int32_t prefetch;       /* 0 default (on), 1 on, -1 off: with the balanced schedule,
-                               bulk-prefetch the index streams (and SDDMM A rows) of
-                               the span a warp takes next into L2                 */
+    int32_t prefetch;       /* 0 default, -1 off, n > 0: bulk-prefetch the B rows of
+                               the batches n ahead into L2 (16-byte vector path)  */
 } spk_tune;
 
 typedef struct spk_csr_s* spk_csr;       /* pattern of S (+ its schedule)      */

@@ -3,11 +3,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <map>
-#include <mutex>
 #include <new>
 #include <string>
-#include <tuple>
 
 #include "common.cuh"
 
@@ -30,25 +27,6 @@ int shape_index(int G, int NV, int U)
 }
 
 Shape shape_at(int i) { return kShapes[i]; }
-
-int64_t resident_ctas(const void* fn, int threads, size_t smem)
-{
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, int, size_t>, int64_t> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(fn, dev, threads, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    int sms = 0, per_sm = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
-        return 0;
-    const int64_t n = (int64_t)sms * per_sm;
-    cache[key] = n;
-    return n;
-}
 
 cudaError_t launch_sddmm(int dta, int dtb, const Launch& L, const SddmmArgs& a, cudaStream_t s)
 {
@@ -249,8 +227,8 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
-// Span-ahead L2 prefetch of index streams: on (1) by default.
-static const int kDefaultPrefetch = 1;
+// Default L2 prefetch distance (batches ahead) of the vector path.
+static const int kDefaultPrefetch = 4;
 
 // Default lane-group shape for a row of nvec 16-byte vectors: 8 lanes per row
 // (one 128-byte line per warp-wide load per row) with up to 4 vectors per
@@ -285,7 +263,7 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     const int threads = (t && t->cta_threads) ? t->cta_threads : 256;
     REQUIRE(threads == 128 || threads == 256, SPK_ERR_ARG, "tune.cta_threads must be 128 or 256");
     const int pf = (t && t->prefetch) ? t->prefetch : kDefaultPrefetch;
-    REQUIRE(pf == -1 || pf == 1, SPK_ERR_ARG, "tune.prefetch must be -1, 0 or 1");
+    REQUIRE(pf == -1 || (pf >= 1 && pf <= 64), SPK_ERR_ARG, "tune.prefetch must be -1, 0 or 1..64");
     L->shape = idx;
     L->vec = vec;
     L->threads = threads;

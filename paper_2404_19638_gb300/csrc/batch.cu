@@ -40,7 +40,7 @@ static const Shape kBatchShapeList[kBatchShapes] = {
 };
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchPrefetch = 0;   // batched units take spans in counter order: no span-ahead prefetch
+constexpr int kBatchPrefetch = 4;   // L2 prefetch distance of batched spans (batches)
 
 // SDDMM: one chunk per warp (groups take interleaved batches of it).
 template <int DT, int G, int NV, int U>

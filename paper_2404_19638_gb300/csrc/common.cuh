@@ -355,11 +355,6 @@ cudaError_t launch_quant_e4m3(const float* X, int64_t M, int64_t K, int64_t ldx,
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// CTAs of `fn` that fit on the whole GPU at once (one wave): SMs times the
-// occupancy at `threads` threads and `smem` bytes (cached per kernel and
-// device; 0 if it cannot be queried).
-int64_t resident_ctas(const void* fn, int threads, size_t smem);
-
 }  // namespace spk
 
 // Host-side handle types (opaque in the C header).

@@ -166,8 +166,6 @@ __global__ void __launch_bounds__(256, min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_
 }
 
 // Vector path: one warp per span (a chunk of the balanced schedule, or a row).
-// The grid is persistent (one wave); with the balanced schedule each warp
-// bulk-prefetches the index streams and A rows of the span it will take next.
 template <int DTA, int DTB, int G, int NV, int U>
 __global__ void __launch_bounds__(256, 3) k_sddmm_lean(const SddmmArgs a)
 {
@@ -175,16 +173,7 @@ __global__ void __launch_bounds__(256, 3) k_sddmm_lean(const SddmmArgs a)
     const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     if (a.bnd) {
-        const unsigned lda_bytes = (unsigned)a.lda * dt_bytes(DTA);
-        auto prefetch = [&](int64_t c) {
-            if (c >= a.nchunks) return;
-            const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-            const int r1 = b1.x < a.M ? b1.x : (int)a.M - 1;
-            prefetch_span_streams(lane, b0.y, b1.y, b0.x, r1, a.colidx, a.rowidx, a.vals, a.A, lda_bytes);
-        };
-        if (a.pf_dist > 0) prefetch(wid);
         for (int64_t c = wid; c < a.nchunks; c += nwarps) {
-            if (a.pf_dist > 0) prefetch(c + nwarps);
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
             sddmm_warp_span<DTA, DTB, G, NV, U, false>(a, lane, b0.x, b0.y, b1.y);
         }
@@ -231,10 +220,8 @@ cudaError_t launch_sddmm_t(const Launch& L, const SddmmArgs& a, cudaStream_t s)
     if (!fn) return cudaErrorInvalidValue;
     const int64_t per_cta = lean ? L.threads / 32 : L.threads / sh.G;     // spans per CTA
     int64_t blocks = (items + per_cta - 1) / per_cta;
-    const size_t smem = lean ? 0 : (size_t)(L.threads / sh.G) * tile_words(sh.G) * sizeof(int);
-    const int64_t wave = resident_ctas(fn, L.threads, smem);
-    if (wave > 0 && blocks > wave) blocks = wave;                 // persistent grid
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    const size_t smem = lean ? 0 : (size_t)(L.threads / sh.G) * tile_words(sh.G) * sizeof(int);
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(L.threads), args, smem, s);
 }

@@ -262,18 +262,7 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 3 : 2) : min_ct
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     int* sm = smem + (threadIdx.x / G) * tile_words(G);
     if (a.bnd) {
-        // persistent grid: each group bulk-prefetches the index streams of
-        // the chunk it will take next
-        const bool pf = (VECN > 1) && a.pf_dist > 0;
-        const float* vstream = a.vals_staged ? a.vals : nullptr;
-        auto prefetch = [&](int64_t c) {
-            if (c >= a.nchunks) return;
-            const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-            prefetch_span_streams(g.gl, b0.y, b1.y, 0, 0, a.colidx, a.rowidx, vstream, nullptr, 0);
-        };
-        if (pf) prefetch(gid);
         for (int64_t c = gid; c < a.nchunks; c += ngroups) {
-            if (pf) prefetch(c + ngroups);
             const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
             const int4 m = a.meta[c];
             if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
@@ -319,11 +308,9 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     if (items <= 0) return cudaSuccess;
     const int64_t groups_per_cta = L.threads / sh.G;
     int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
     if (nkb > 65535) return cudaErrorInvalidValue;
     const size_t smem = L.vec ? 0 : (size_t)groups_per_cta * tile_words(sh.G) * sizeof(int);
-    const int64_t wave = resident_ctas(fn, L.threads, smem) / nkb;
-    if (wave > 0 && blocks > wave) blocks = wave;                 // persistent grid
-    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)nkb), dim3(L.threads), args, smem, s);
 }
