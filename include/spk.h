@@ -72,9 +72,7 @@ typedef struct spk_tune {
     int32_t group_lanes;    /* lanes that share one row of the dense factor: 4, 8, 16, 32 */
     int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
     int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
-    int32_t cta_threads;    /* threads per CTA: 128, 256                           */
-    int32_t prefetch;       /* 0 default, -1 off, n > 0: bulk-prefetch the B rows of
-                               the batches n ahead into L2 (16-byte vector path)  */
+    int32_t cta_threads;    /* threads per CTA: 128, 256, 512                      */
 } spk_tune;
 
 typedef struct spk_csr_s* spk_csr;       /* pattern of S (+ its schedule)      */

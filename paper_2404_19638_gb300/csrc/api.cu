@@ -227,9 +227,6 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
-// Default L2 prefetch distance (batches ahead) of the vector path.
-static const int kDefaultPrefetch = 4;
-
 // Default lane-group shape for a row of nvec 16-byte vectors: 8 lanes per row
 // (one 128-byte line per warp-wide load per row) with up to 4 vectors per
 // lane, 4 nonzeros in flight per group.
@@ -262,13 +259,10 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
             G, NV, U);
     const int threads = (t && t->cta_threads) ? t->cta_threads : 256;
     REQUIRE(threads == 128 || threads == 256, SPK_ERR_ARG, "tune.cta_threads must be 128 or 256");
-    const int pf = (t && t->prefetch) ? t->prefetch : kDefaultPrefetch;
-    REQUIRE(pf == -1 || (pf >= 1 && pf <= 64), SPK_ERR_ARG, "tune.prefetch must be -1, 0 or 1..64");
     L->shape = idx;
     L->vec = vec;
     L->threads = threads;
     L->chunks = (variant == 2);
-    L->pf_dist = pf > 0 ? pf : 0;
     return SPK_OK;
 }
 
@@ -287,7 +281,6 @@ extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int3
     out->vecs_per_lane = sh.NV;
     out->unroll = sh.U;
     out->cta_threads = L.threads;
-    out->prefetch = L.pf_dist > 0 ? L.pf_dist : -1;
     return SPK_OK;
 }
 
@@ -323,7 +316,6 @@ extern "C" spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2
     a.out = out;
     a.bnd = L.chunks ? S->bnd : nullptr;
     a.nchunks = S->nchunks;
-    a.pf_dist = L.pf_dist;
     cudaError_t e = launch_sddmm(dta, dtb, L, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "spk_sddmm launch");
     return SPK_OK;
@@ -377,7 +369,6 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
     a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
     a.carry = reinterpret_cast<float*>(ws);
     a.nchunks = S->nchunks;
-    a.pf_dist = L.pf_dist;
     cudaError_t e = launch_spmm(dtb, L, a, stream);
     if (e != cudaSuccess) return cuda_fail(e, name);
     return SPK_OK;

@@ -40,7 +40,6 @@ static const Shape kBatchShapeList[kBatchShapes] = {
 };
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchPrefetch = 4;   // L2 prefetch distance of batched spans (batches)
 
 // SDDMM: one chunk per warp (groups take interleaved batches of it).
 template <int DT, int G, int NV, int U>
@@ -214,7 +213,6 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
             a.B = it.B; a.ldb = it.ldb; a.b_scale = nullptr;
             a.out = reinterpret_cast<float*>(it.out);
             a.bnd = S->bnd; a.nchunks = S->nchunks;
-            a.pf_dist = kBatchPrefetch;
             P.unit_begin[m + 1] = units + (S->nnz > 0 ? S->nchunks : 0);     // one chunk per warp
         } else {
             d.nkb = (nvec + G * NV - 1) / (G * NV);
@@ -228,7 +226,6 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
             a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
             a.carry = nullptr;   // set at create time
             a.nchunks = S->nchunks;
-            a.pf_dist = kBatchPrefetch;
             P.carry_off[m] = carry;
             carry += align256((size_t)S->npieces * it.K * 4);
             P.unit_begin[m + 1] = units + (S->M > 0 ? wunits * d.nkb : 0);

@@ -254,7 +254,6 @@ struct SddmmArgs {
     float* out;
     const int2* bnd;          // chunk boundaries (row, nonzero); NULL = row-split
     int64_t nchunks;
-    int32_t pf_dist;          // L2 prefetch distance in batches (0 = off)
 };
 
 struct SpmmArgs {
@@ -276,7 +275,6 @@ struct SpmmArgs {
     int32_t* cnt;             // arrival counters per split row (self-resetting)
     float* carry;             // partial rows, K floats per slot
     int64_t nchunks;
-    int32_t pf_dist;          // L2 prefetch distance in batches (0 = off)
 };
 
 // Kernel shape: lanes per group, 16-byte vectors per lane, nonzeros in flight.
@@ -307,7 +305,6 @@ struct Launch {
     bool vec;          // 16-byte vector mode (else one element per lane slot)
     int threads;
     bool chunks;       // balanced schedule
-    int pf_dist;       // L2 prefetch distance in batches (0 = off)
 };
 
 // Launchers (one per dtype family; defined in the sddmm_*.cu / spmm_*.cu files).

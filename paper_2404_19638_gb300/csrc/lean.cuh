@@ -22,14 +22,6 @@ __device__ __forceinline__ unsigned group_mask(int lane)
     return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte
-// aligned).  Nothing waits for it: it only turns later gathers of a row that
-// is not yet in L2 into L2 hits.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Four consecutive int32 (or float) entries at a 16-byte aligned position.
 __device__ __forceinline__ int4 ld4(const int32_t* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
 
@@ -90,31 +82,7 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
     };
     const int wb0 = e0 & ~3;
     if (wb0 + grp * U < e1) load_idx(wb0 + grp * U);
-    // L2 prefetch, pf_dist warp batches ahead: lane l covers nonzero
-    // wb + dist*WB + l; its index is loaded one iteration before it is used.
-    const int dist = a.pf_dist;
-    const unsigned brow_bytes = (unsigned)a.K * dt_bytes(DTB);
-    const unsigned arow_bytes = (unsigned)a.K * dt_bytes(DTA);
-    int pj = -1, pr = -1;
-    auto load_pf = [&](int wbx) {
-        const int e = wbx + dist * WB + lane;
-        pj = -1;
-        if (lane < WB && e >= e0 && e < e1) {
-            pj = __ldg(a.colidx + e);
-            if constexpr (!KNOWN_ROW) pr = __ldg(a.rowidx + e);
-        }
-    };
-    if (dist > 0) load_pf(wb0);
     for (int wb = wb0; wb < e1; wb += WB) {
-        if (dist > 0) {
-            if (pj >= 0) prefetch_l2(Bb + (size_t)(unsigned)pj * ldb_bytes, brow_bytes);
-            if constexpr (!KNOWN_ROW) {
-                const int prev = __shfl_up_sync(0xffffffffu, pj >= 0 ? pr : -1, 1);
-                if (pj >= 0 && (lane == 0 || pr != prev))
-                    prefetch_l2(Ab + (size_t)(unsigned)pr * lda_bytes, arow_bytes);
-            }
-            load_pf(wb + WB);
-        }
         const int eg = wb + grp * U;
         if (eg >= e1) continue;
         const bool full = nfull;
@@ -297,26 +265,10 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             }
         }
     };
-    // L2 prefetch, pf_dist batches ahead: lane gl < U covers nonzero
-    // eb + dist*U + gl; its index is loaded one iteration before it is used.
-    const int dist = a.pf_dist;
-    const unsigned brow_bytes = (unsigned)a.K * dt_bytes(DTB);
-    int pj = -1;
-    auto load_pf = [&](int ebx) {
-        const int e = ebx + dist * U + gl;
-        pj = (gl < U && e >= e0 && e < e1) ? __ldg(a.colidx + e) : -1;
-    };
     // An empty span (e0 == e1) still rounds down to a batch start below e1:
     // it must not enter the loop, whose indices come from load_idx.
-    if (e0 < e1) {
-        load_idx(e0 & ~3);
-        if (dist > 0) load_pf(e0 & ~3);
-    }
+    if (e0 < e1) load_idx(e0 & ~3);
     for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
-        if (dist > 0) {
-            if (pj >= 0) prefetch_l2(Bb + (size_t)(unsigned)pj * ldb_bytes, brow_bytes);
-            load_pf(eb + U);
-        }
         const bool full = nfull;
         int j[U], row[U];
         float s[U];
