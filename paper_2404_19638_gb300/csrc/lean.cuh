@@ -47,6 +47,8 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
     bool vin[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) vin[t] = (t * G + gl) < nvec;
+    const bool all_vin = (nvec >= G * NV);                     // no lane has a vector past K
+    const unsigned lane_off = (unsigned)gl * 16u;              // byte offset of the lane's first vector
 
     float av[NV][VECN];
     int cur = -1;
@@ -97,33 +99,44 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
             sv = a.vals ? __ldg(a.vals + ew) : 1.f;
             if (a.vals2) sv *= __ldg(a.vals2 + ew);
         }
-        Raw<DTB, VECN> bw[U][NV];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
-#pragma unroll
-            for (int t = 0; t < NV; ++t) {
-                if ((full || j[u] >= 0) && vin[t])
-                    load_raw<DTB, VECN>(brow, (int64_t)(t * G + gl) * VECN, bw[u][t]);
-                else
-                    zero_raw(bw[u][t]);
-            }
-        }
         if (eg + WB < e1) load_idx(eg + WB);
         float p[U];
-        if (full && row[0] == cur && row[U - 1] == cur) {
+        if (full && all_vin && row[0] == cur && row[U - 1] == cur) {
+            // Common case: U valid nonzeros of the current row, every lane's
+            // vectors inside K: unconditional loads, one address per row.
+            uint4 bw[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes + lane_off);
+#pragma unroll
+                for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 p[u] = 0.f;
 #pragma unroll
                 for (int t = 0; t < NV; ++t) {
+                    Raw<DTB, VECN> rb;
+                    rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
                     float bf[VECN];
-                    unpack_all<DTB, VECN>(bw[u][t], bf);
+                    unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
                     for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
                 }
             }
         } else {
+            Raw<DTB, VECN> bw[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
+#pragma unroll
+                for (int t = 0; t < NV; ++t) {
+                    if ((full || j[u] >= 0) && vin[t])
+                        load_raw<DTB, VECN>(brow, (int64_t)(t * G + gl) * VECN, bw[u][t]);
+                    else
+                        zero_raw(bw[u][t]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 p[u] = 0.f;
@@ -198,6 +211,8 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
     bool vin[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) vin[t] = (vbase + t * G + gl) < nvec;
+    const bool all_vin = (nvec >= vbase + G * NV);            // no lane has a vector past this K block
+    const unsigned lane_off = (unsigned)(vbase + gl) * 16u;   // byte offset of the lane's first vector
     const bool vec_vals = a.vals_staged != 0;            // vals alone, 16-byte aligned
 
     float acc[NV][VECN];
@@ -279,30 +294,41 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             for (int u = 0; u < U; ++u)
                 if (full || j[u] >= 0) s[u] *= __ldg(a.b_scale + j[u]);
         }
-        Raw<DTB, VECN> bw[U][NV];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
-#pragma unroll
-            for (int t = 0; t < NV; ++t) {
-                if ((full || j[u] >= 0) && vin[t])
-                    load_raw<DTB, VECN>(brow, (int64_t)(vbase + t * G + gl) * VECN, bw[u][t]);
-                else
-                    zero_raw(bw[u][t]);
-            }
-        }
         if (eb + U < e1) load_idx(eb + U);
-        if (full && (KNOWN_ROW || row[U - 1] == cur)) {
+        if (full && all_vin && (KNOWN_ROW || row[U - 1] == cur)) {
+            // Common case: U valid nonzeros of the current row, every lane's
+            // vectors inside this K block: unconditional loads.
+            uint4 bw[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes + lane_off);
+#pragma unroll
+                for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int t = 0; t < NV; ++t) {
+                    Raw<DTB, VECN> rb;
+                    rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
                     float bf[VECN];
-                    unpack_all<DTB, VECN>(bw[u][t], bf);
+                    unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
                     for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bf[q], acc[t][q]);
                 }
         } else {
+            Raw<DTB, VECN> bw[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
+#pragma unroll
+                for (int t = 0; t < NV; ++t) {
+                    if ((full || j[u] >= 0) && vin[t])
+                        load_raw<DTB, VECN>(brow, (int64_t)(vbase + t * G + gl) * VECN, bw[u][t]);
+                    else
+                        zero_raw(bw[u][t]);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (!full && j[u] < 0) continue;
