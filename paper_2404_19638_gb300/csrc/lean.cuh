@@ -29,6 +29,11 @@ __device__ __forceinline__ int4 ld4(const int32_t* p) { return __ldg(reinterpret
 // SDDMM: a warp walks a span of nonzeros in warp batches of (32/G)*U; group k
 // of the warp takes nonzeros [wb + kU, wb + kU + U).  Outputs are per nonzero,
 // so the groups never combine results.
+//
+// Registers bound the gathers in flight (resident warps x U rows), so the hot
+// path keeps only the U gathered vectors, the A slice and U partial sums live.
+// A batch that is full, inside K and in the current row takes the fast path;
+// anything else (span edges, row changes) goes nonzero by nonzero.
 // ----------------------------------------------------------------------------
 template <int DTA, int DTB, int G, int NV, int U, bool KNOWN_ROW>
 __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, int r0, int e0, int e1)
@@ -40,147 +45,117 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
     const int grp = lane / G, gl = lane % G;
     const unsigned gmask = group_mask<G>(lane);
     const int nvec = a.K / VECN;
-    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B);
+    const bool all_vin = (nvec >= G * NV);
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + gl * 16;   // lane's first vector
     const char* __restrict__ Ab = reinterpret_cast<const char*>(a.A);
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DTB);
     const unsigned lda_bytes = (unsigned)a.lda * dt_bytes(DTA);
-    bool vin[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) vin[t] = (t * G + gl) < nvec;
-    const bool all_vin = (nvec >= G * NV);                     // no lane has a vector past K
-    const unsigned lane_off = (unsigned)gl * 16u;              // byte offset of the lane's first vector
 
     float av[NV][VECN];
     int cur = -1;
-    // Indices of the next batch are loaded while the current batch's rows are
-    // being gathered, so a batch costs one memory round trip, not two.
-    int nj[U], nrow[U];
-    bool nfull = false;
-    auto load_idx = [&](int eg) {
-        nfull = (eg >= e0) && (eg + U <= e1);
-        if (nfull) {
+    auto load_a = [&](int r) {
+        const char* arow = Ab + (size_t)(unsigned)r * lda_bytes;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            if (t * G + gl < nvec) load_elems<DTA, VECN>(arow, (int64_t)(t * G + gl) * VECN, av[t]);
+            else
+#pragma unroll
+                for (int q = 0; q < VECN; ++q) av[t][q] = 0.f;
+        }
+    };
+    for (int wb = e0 & ~3; wb < e1; wb += WB) {
+        const int eg = wb + grp * U;
+        if (eg >= e1) continue;
+        if (all_vin && eg >= e0 && eg + U <= e1) {
+            int j[U], row[U];
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eg + u);
-                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
+                j[u] = c.x; j[u + 1] = c.y; j[u + 2] = c.z; j[u + 3] = c.w;
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eg + u);
-                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
+                    row[u] = r.x; row[u + 1] = r.y; row[u + 2] = r.z; row[u + 3] = r.w;
+                } else {
+                    row[u] = row[u + 1] = row[u + 2] = row[u + 3] = r0;
                 }
             }
-        } else {
+            if (row[U - 1] == cur || (row[0] == row[U - 1])) {
+                // fast path: one row for the whole batch, every vector inside K
+                uint4 bw[U][NV];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = eg + u;
-                const bool ok = (e >= e0) && (e < e1);
-                nj[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
-            }
-        }
-        if constexpr (KNOWN_ROW) {
+                for (int u = 0; u < U; ++u) {
+                    const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
 #pragma unroll
-            for (int u = 0; u < U; ++u) nrow[u] = r0;
-        }
-    };
-    const int wb0 = e0 & ~3;
-    if (wb0 + grp * U < e1) load_idx(wb0 + grp * U);
-    for (int wb = wb0; wb < e1; wb += WB) {
-        const int eg = wb + grp * U;
-        if (eg >= e1) continue;
-        const bool full = nfull;
-        int j[U], row[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; }
-        // the lane that stores nonzero eg + gl fetches its scale early
-        const int ew = eg + gl;
-        const bool writer = (gl < U) && (ew >= e0) && (ew < e1);
-        float sv = 0.f;
-        if (writer) {
-            sv = a.vals ? __ldg(a.vals + ew) : 1.f;
-            if (a.vals2) sv *= __ldg(a.vals2 + ew);
-        }
-        if (eg + WB < e1) load_idx(eg + WB);
-        float p[U];
-        if (full && all_vin && row[0] == cur && row[U - 1] == cur) {
-            // Common case: U valid nonzeros of the current row, every lane's
-            // vectors inside K: unconditional loads, one address per row.
-            uint4 bw[U][NV];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes + lane_off);
-#pragma unroll
-                for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                p[u] = 0.f;
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    Raw<DTB, VECN> rb;
-                    rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
-                    float bf[VECN];
-                    unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                    for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
+                    for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
                 }
-            }
-        } else {
-            Raw<DTB, VECN> bw[U][NV];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    if ((full || j[u] >= 0) && vin[t])
-                        load_raw<DTB, VECN>(brow, (int64_t)(t * G + gl) * VECN, bw[u][t]);
-                    else
-                        zero_raw(bw[u][t]);
+                float sv = 1.f;
+                if (gl < U) {
+                    if (a.vals) sv = __ldg(a.vals + eg + gl);
+                    if (a.vals2) sv *= __ldg(a.vals2 + eg + gl);
                 }
-            }
+                if (row[0] != cur) { cur = row[0]; load_a(cur); }
+                float p[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                p[u] = 0.f;
-                if (!full && j[u] < 0) continue;
-                if (row[u] != cur) {
-                    cur = row[u];
-                    const char* arow = Ab + (size_t)(unsigned)cur * lda_bytes;
+                for (int u = 0; u < U; ++u) {
+                    p[u] = 0.f;
 #pragma unroll
                     for (int t = 0; t < NV; ++t) {
-                        if (vin[t]) load_elems<DTA, VECN>(arow, (int64_t)(t * G + gl) * VECN, av[t]);
-                        else
+                        Raw<DTB, VECN> rb;
+                        rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
+                        float bf[VECN];
+                        unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
-                            for (int q = 0; q < VECN; ++q) av[t][q] = 0.f;
+                        for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
+                    }
+                    if constexpr (DTA == DT_E4M3) p[u] *= __ldg(a.a_scale + cur) * __ldg(a.b_scale + j[u]);
+                }
+                // Reduce-scatter over the low log2(U) lane bits, then butterflies
+                // over the remaining G/U lane subsets: nonzero eg + (gl % U) ends
+                // in lane gl.
+#pragma unroll
+                for (int d = U / 2; d >= 1; d >>= 1) {
+                    const bool upper = (gl & d) != 0;
+#pragma unroll
+                    for (int i = 0; i < d; ++i) {
+                        const float send = upper ? p[i] : p[i + d];
+                        const float keep = upper ? p[i + d] : p[i];
+                        p[i] = keep + __shfl_xor_sync(gmask, send, d, G);
                     }
                 }
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    float bf[VECN];
-                    unpack_all<DTB, VECN>(bw[u][t], bf);
+                for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(gmask, p[0], d, G);
+                if (gl < U) __stcs(a.out + eg + gl, sv * p[0]);
+                continue;
+            }
+        }
+        // general path: one nonzero at a time (span edges, row changes, K tails)
+#pragma unroll 1
+        for (int u = 0; u < U; ++u) {
+            const int e = eg + u;
+            if (e < e0 || e >= e1) continue;
+            const int j = __ldg(a.colidx + e);
+            const int r = KNOWN_ROW ? r0 : __ldg(a.rowidx + e);
+            if (r != cur) { cur = r; load_a(cur); }
+            const char* brow = Bb + (size_t)(unsigned)j * ldb_bytes;
+            float p = 0.f;
 #pragma unroll
-                    for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
+            for (int t = 0; t < NV; ++t) {
+                if (t * G + gl < nvec) {
+                    float bf[VECN];
+                    load_elems<DTB, VECN>(brow, (int64_t)t * G * VECN, bf);
+#pragma unroll
+                    for (int q = 0; q < VECN; ++q) p = fmaf(av[t][q], bf[q], p);
                 }
             }
-        }
-        if constexpr (DTA == DT_E4M3) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (full || j[u] >= 0) p[u] *= __ldg(a.a_scale + row[u]) * __ldg(a.b_scale + j[u]);
-        }
-        // Reduce-scatter over the low log2(U) lane bits, then butterflies over
-        // the remaining G/U lane subsets: nonzero eg + (gl % U) ends in lane gl.
-#pragma unroll
-        for (int d = U / 2; d >= 1; d >>= 1) {
-            const bool upper = (gl & d) != 0;
-#pragma unroll
-            for (int i = 0; i < d; ++i) {
-                const float send = upper ? p[i] : p[i + d];
-                const float keep = upper ? p[i + d] : p[i];
-                p[i] = keep + __shfl_xor_sync(gmask, send, d, G);
+            for (int d = 1; d < G; d <<= 1) p += __shfl_xor_sync(gmask, p, d, G);
+            if constexpr (DTA == DT_E4M3) p *= __ldg(a.a_scale + r) * __ldg(a.b_scale + j);
+            if (gl == 0) {
+                float sv = a.vals ? __ldg(a.vals + e) : 1.f;
+                if (a.vals2) sv *= __ldg(a.vals2 + e);
+                __stcs(a.out + e, sv * p);
             }
         }
-#pragma unroll
-        for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(gmask, p[0], d, G);
-        if (writer) __stcs(a.out + ew, sv * p[0]);
     }
 }
 
@@ -206,13 +181,9 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
     const int gl = g.gl;
     const int nvec = a.K / VECN;
     const int vbase = kb * G * NV;
-    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B);
+    const bool all_vin = (nvec >= vbase + G * NV);
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (vbase + gl) * 16;   // lane's first vector
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DTB);
-    bool vin[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) vin[t] = (vbase + t * G + gl) < nvec;
-    const bool all_vin = (nvec >= vbase + G * NV);            // no lane has a vector past this K block
-    const unsigned lane_off = (unsigned)(vbase + gl) * 16u;   // byte offset of the lane's first vector
     const bool vec_vals = a.vals_staged != 0;            // vals alone, 16-byte aligned
 
     float acc[NV][VECN];
@@ -229,126 +200,89 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
         else
             write_row<VECN, G, NV>(a, g, kb, nvec, row, acc);
     };
+    auto value = [&](int e) {
+        const int vi = a.vperm ? __ldg(a.vperm + e) : e;
+        float sv = a.vals ? __ldg(a.vals + vi) : 1.f;
+        if (a.vals2) sv *= __ldg(a.vals2 + vi);
+        return sv;
+    };
 
-    // Indices and values of the next batch are loaded while the current
-    // batch's rows are being gathered (one memory round trip per batch).
-    int nj[U], nrow[U];
-    float ns[U];
-    bool nfull = false;
-    auto load_idx = [&](int eb) {
-        nfull = (eb >= e0) && (eb + U <= e1);
-        if (nfull) {
+    // An empty span (e0 == e1) still rounds down to a batch start below e1:
+    // it must not enter the loop.
+    for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
+        if (all_vin && eb >= e0 && eb + U <= e1) {
+            int j[U], last_row;
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eb + u);
-                nj[u] = c.x; nj[u + 1] = c.y; nj[u + 2] = c.z; nj[u + 3] = c.w;
-                if constexpr (!KNOWN_ROW) {
-                    const int4 r = ld4(a.rowidx + eb + u);
-                    nrow[u] = r.x; nrow[u + 1] = r.y; nrow[u + 2] = r.z; nrow[u + 3] = r.w;
+                j[u] = c.x; j[u + 1] = c.y; j[u + 2] = c.z; j[u + 3] = c.w;
+            }
+            if constexpr (KNOWN_ROW) last_row = r0;
+            else last_row = __ldg(a.rowidx + eb + U - 1);
+            if (last_row == cur) {
+                // fast path: U nonzeros of the current row, every vector inside this K block
+                uint4 bw[U][NV];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
                 }
-            }
-        } else {
+                float s[U];
+                if (vec_vals) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = eb + u;
-                const bool ok = (e >= e0) && (e < e1);
-                nj[u] = ok ? __ldg(a.colidx + e) : -1;
-                if constexpr (!KNOWN_ROW) nrow[u] = ok ? __ldg(a.rowidx + e) : -1;
-            }
-        }
-        if constexpr (KNOWN_ROW) {
+                    for (int u = 0; u < U; u += 4) {
+                        const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
+                        s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
+                    }
+                } else {
 #pragma unroll
-            for (int u = 0; u < U; ++u) nrow[u] = r0;
-        }
-        if (nfull && vec_vals) {
-#pragma unroll
-            for (int u = 0; u < U; u += 4) {
-                const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
-                ns[u] = v4.x; ns[u + 1] = v4.y; ns[u + 2] = v4.z; ns[u + 3] = v4.w;
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float sv = 0.f;
-                if (nfull || nj[u] >= 0) {
-                    const int e = eb + u;
-                    const int vi = a.vperm ? __ldg(a.vperm + e) : e;
-                    sv = a.vals ? __ldg(a.vals + vi) : 1.f;
-                    if (a.vals2) sv *= __ldg(a.vals2 + vi);
+                    for (int u = 0; u < U; ++u) s[u] = value(eb + u);
                 }
-                ns[u] = sv;
-            }
-        }
-    };
-    // An empty span (e0 == e1) still rounds down to a batch start below e1:
-    // it must not enter the loop, whose indices come from load_idx.
-    if (e0 < e1) load_idx(e0 & ~3);
-    for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
-        const bool full = nfull;
-        int j[U], row[U];
-        float s[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) { j[u] = nj[u]; row[u] = nrow[u]; s[u] = ns[u]; }
-        if constexpr (DTB == DT_E4M3) {
+                for (int u = 0; u < U; ++u) {
+                    if constexpr (DTB == DT_E4M3) s[u] *= __ldg(a.b_scale + j[u]);
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (full || j[u] >= 0) s[u] *= __ldg(a.b_scale + j[u]);
-        }
-        if (eb + U < e1) load_idx(eb + U);
-        if (full && all_vin && (KNOWN_ROW || row[U - 1] == cur)) {
-            // Common case: U valid nonzeros of the current row, every lane's
-            // vectors inside this K block: unconditional loads.
-            uint4 bw[U][NV];
+                    for (int t = 0; t < NV; ++t) {
+                        Raw<DTB, VECN> rb;
+                        rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
+                        float bf[VECN];
+                        unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes + lane_off);
-#pragma unroll
-                for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    Raw<DTB, VECN> rb;
-                    rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
-                    float bf[VECN];
-                    unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                    for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bf[q], acc[t][q]);
-                }
-        } else {
-            Raw<DTB, VECN> bw[U][NV];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
-#pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    if ((full || j[u] >= 0) && vin[t])
-                        load_raw<DTB, VECN>(brow, (int64_t)(vbase + t * G + gl) * VECN, bw[u][t]);
-                    else
-                        zero_raw(bw[u][t]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (!full && j[u] < 0) continue;
-                if constexpr (!KNOWN_ROW) {
-                    if (row[u] != cur) {
-                        flush(cur);
-                        for (int rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
-                        cur = row[u];
-#pragma unroll
-                        for (int t = 0; t < NV; ++t)
-#pragma unroll
-                            for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
+                        for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bf[q], acc[t][q]);
                     }
                 }
+                continue;
+            }
+        }
+        // general path: one nonzero at a time (span edges, row changes, K tails)
+#pragma unroll 1
+        for (int u = 0; u < U; ++u) {
+            const int e = eb + u;
+            if (e < e0 || e >= e1) continue;
+            const int j = __ldg(a.colidx + e);
+            if constexpr (!KNOWN_ROW) {
+                const int r = __ldg(a.rowidx + e);
+                if (r != cur) {
+                    flush(cur);
+                    for (int rr = cur + 1; rr < r; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
+                    cur = r;
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
+                    for (int t = 0; t < NV; ++t)
+#pragma unroll
+                        for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
+                }
+            }
+            float sv = value(e);
+            if constexpr (DTB == DT_E4M3) sv *= __ldg(a.b_scale + j);
+            const char* brow = Bb + (size_t)(unsigned)j * ldb_bytes;
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                if (vbase + t * G + gl < nvec) {
                     float bf[VECN];
-                    unpack_all<DTB, VECN>(bw[u][t], bf);
+                    load_elems<DTB, VECN>(brow, (int64_t)t * G * VECN, bf);
 #pragma unroll
-                    for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bf[q], acc[t][q]);
+                    for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(sv, bf[q], acc[t][q]);
                 }
             }
         }
