@@ -63,11 +63,19 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
                 for (int q = 0; q < VECN; ++q) av[t][q] = 0.f;
         }
     };
+    bool vin[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) vin[t] = all_vin || (t * G + gl < nvec);
     for (int wb = e0 & ~3; wb < e1; wb += WB) {
         const int eg = wb + grp * U;
         if (eg >= e1) continue;
-        if (all_vin && eg >= e0 && eg + U <= e1) {
-            int j[U], row[U];
+        // One batch body for every case; invalid slots, row changes and K tails
+        // are predicates, so the lock-stepped groups of a warp never run two
+        // different code paths one after the other.
+        const bool full = (eg >= e0) && (eg + U <= e1);
+        int j[U], row[U];
+        bool ok[U];
+        if (full) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eg + u);
@@ -75,87 +83,71 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
                 if constexpr (!KNOWN_ROW) {
                     const int4 r = ld4(a.rowidx + eg + u);
                     row[u] = r.x; row[u + 1] = r.y; row[u + 2] = r.z; row[u + 3] = r.w;
-                } else {
-                    row[u] = row[u + 1] = row[u + 2] = row[u + 3] = r0;
                 }
             }
-            if (row[U - 1] == cur || (row[0] == row[U - 1])) {
-                // fast path: one row for the whole batch, every vector inside K
-                uint4 bw[U][NV];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+            for (int u = 0; u < U; ++u) ok[u] = true;
+        } else {
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
-                }
-                float sv = 1.f;
-                if (gl < U) {
-                    if (a.vals) sv = __ldg(a.vals + eg + gl);
-                    if (a.vals2) sv *= __ldg(a.vals2 + eg + gl);
-                }
-                if (row[0] != cur) { cur = row[0]; load_a(cur); }
-                float p[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    p[u] = 0.f;
-#pragma unroll
-                    for (int t = 0; t < NV; ++t) {
-                        Raw<DTB, VECN> rb;
-                        rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
-                        float bf[VECN];
-                        unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
-                    }
-                    if constexpr (DTA == DT_E4M3) p[u] *= __ldg(a.a_scale + cur) * __ldg(a.b_scale + j[u]);
-                }
-                // Reduce-scatter over the low log2(U) lane bits, then butterflies
-                // over the remaining G/U lane subsets: nonzero eg + (gl % U) ends
-                // in lane gl.
-#pragma unroll
-                for (int d = U / 2; d >= 1; d >>= 1) {
-                    const bool upper = (gl & d) != 0;
-#pragma unroll
-                    for (int i = 0; i < d; ++i) {
-                        const float send = upper ? p[i] : p[i + d];
-                        const float keep = upper ? p[i + d] : p[i];
-                        p[i] = keep + __shfl_xor_sync(gmask, send, d, G);
-                    }
-                }
-#pragma unroll
-                for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(gmask, p[0], d, G);
-                if (gl < U) __stcs(a.out + eg + gl, sv * p[0]);
-                continue;
+            for (int u = 0; u < U; ++u) {
+                const int e = eg + u;
+                ok[u] = (e >= e0) && (e < e1);
+                j[u] = ok[u] ? __ldg(a.colidx + e) : 0;
+                if constexpr (!KNOWN_ROW) row[u] = ok[u] ? __ldg(a.rowidx + e) : cur;
             }
         }
-        // general path: one nonzero at a time (span edges, row changes, K tails)
-#pragma unroll 1
+        if constexpr (KNOWN_ROW) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) row[u] = r0;
+        }
+        uint4 bw[U][NV];
+#pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int e = eg + u;
-            if (e < e0 || e >= e1) continue;
-            const int j = __ldg(a.colidx + e);
-            const int r = KNOWN_ROW ? r0 : __ldg(a.rowidx + e);
-            if (r != cur) { cur = r; load_a(cur); }
-            const char* brow = Bb + (size_t)(unsigned)j * ldb_bytes;
-            float p = 0.f;
+            const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                if (ok[u] && vin[t]) bw[u][t] = __ldg(brow + t * G);
+        }
+        float sv = 1.f;
+        const int ew = eg + gl;
+        const bool writer = (gl < U) && (ew >= e0) && (ew < e1);
+        if (writer) {
+            if (a.vals) sv = __ldg(a.vals + ew);
+            if (a.vals2) sv *= __ldg(a.vals2 + ew);
+        }
+        float p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            p[u] = 0.f;
+            if (!ok[u]) continue;
+            if (row[u] != cur) { cur = row[u]; load_a(cur); }
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
-                if (t * G + gl < nvec) {
-                    float bf[VECN];
-                    load_elems<DTB, VECN>(brow, (int64_t)t * G * VECN, bf);
+                if (!vin[t]) continue;
+                Raw<DTB, VECN> rb;
+                rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
+                float bf[VECN];
+                unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
-                    for (int q = 0; q < VECN; ++q) p = fmaf(av[t][q], bf[q], p);
-                }
+                for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
             }
+            if constexpr (DTA == DT_E4M3) p[u] *= __ldg(a.a_scale + cur) * __ldg(a.b_scale + j[u]);
+        }
+        // Reduce-scatter over the low log2(U) lane bits, then butterflies over
+        // the remaining G/U lane subsets: nonzero eg + (gl % U) ends in lane gl.
 #pragma unroll
-            for (int d = 1; d < G; d <<= 1) p += __shfl_xor_sync(gmask, p, d, G);
-            if constexpr (DTA == DT_E4M3) p *= __ldg(a.a_scale + r) * __ldg(a.b_scale + j);
-            if (gl == 0) {
-                float sv = a.vals ? __ldg(a.vals + e) : 1.f;
-                if (a.vals2) sv *= __ldg(a.vals2 + e);
-                __stcs(a.out + e, sv * p);
+        for (int d = U / 2; d >= 1; d >>= 1) {
+            const bool upper = (gl & d) != 0;
+#pragma unroll
+            for (int i = 0; i < d; ++i) {
+                const float send = upper ? p[i] : p[i + d];
+                const float keep = upper ? p[i + d] : p[i];
+                p[i] = keep + __shfl_xor_sync(gmask, send, d, G);
             }
         }
+#pragma unroll
+        for (int d = U; d < G; d <<= 1) p[0] += __shfl_xor_sync(gmask, p[0], d, G);
+        if (writer) __stcs(a.out + ew, sv * p[0]);
     }
 }
 
@@ -207,83 +199,86 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
         return sv;
     };
 
+    bool vin[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) vin[t] = all_vin || (vbase + t * G + gl < nvec);
     // An empty span (e0 == e1) still rounds down to a batch start below e1:
     // it must not enter the loop.
     for (int eb = e0 & ~3; e0 < e1 && eb < e1; eb += U) {
-        if (all_vin && eb >= e0 && eb + U <= e1) {
-            int j[U], last_row;
+        // One batch body for every case (see sddmm_warp_span).
+        const bool full = (eb >= e0) && (eb + U <= e1);
+        int j[U], row[U];
+        bool ok[U];
+        float s[U];
+        if (full) {
 #pragma unroll
             for (int u = 0; u < U; u += 4) {
                 const int4 c = ld4(a.colidx + eb + u);
                 j[u] = c.x; j[u + 1] = c.y; j[u + 2] = c.z; j[u + 3] = c.w;
+                if constexpr (!KNOWN_ROW) {
+                    const int4 r = ld4(a.rowidx + eb + u);
+                    row[u] = r.x; row[u + 1] = r.y; row[u + 2] = r.z; row[u + 3] = r.w;
+                }
             }
-            if constexpr (KNOWN_ROW) last_row = r0;
-            else last_row = __ldg(a.rowidx + eb + U - 1);
-            if (last_row == cur) {
-                // fast path: U nonzeros of the current row, every vector inside this K block
-                uint4 bw[U][NV];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+            for (int u = 0; u < U; ++u) ok[u] = true;
+            if (vec_vals) {
 #pragma unroll
-                    for (int t = 0; t < NV; ++t) bw[u][t] = __ldg(brow + t * G);
+                for (int u = 0; u < U; u += 4) {
+                    const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
+                    s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
                 }
-                float s[U];
-                if (vec_vals) {
+            } else {
 #pragma unroll
-                    for (int u = 0; u < U; u += 4) {
-                        const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
-                        s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
-                    }
-                } else {
+                for (int u = 0; u < U; ++u) s[u] = value(eb + u);
+            }
+        } else {
 #pragma unroll
-                    for (int u = 0; u < U; ++u) s[u] = value(eb + u);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if constexpr (DTB == DT_E4M3) s[u] *= __ldg(a.b_scale + j[u]);
-#pragma unroll
-                    for (int t = 0; t < NV; ++t) {
-                        Raw<DTB, VECN> rb;
-                        rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
-                        float bf[VECN];
-                        unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                        for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(s[u], bf[q], acc[t][q]);
-                    }
-                }
-                continue;
+            for (int u = 0; u < U; ++u) {
+                const int e = eb + u;
+                ok[u] = (e >= e0) && (e < e1);
+                j[u] = ok[u] ? __ldg(a.colidx + e) : 0;
+                if constexpr (!KNOWN_ROW) row[u] = ok[u] ? __ldg(a.rowidx + e) : cur;
+                s[u] = ok[u] ? value(e) : 0.f;
             }
         }
-        // general path: one nonzero at a time (span edges, row changes, K tails)
-#pragma unroll 1
+        if constexpr (KNOWN_ROW) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) row[u] = r0;
+        }
+        uint4 bw[U][NV];
+#pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int e = eb + u;
-            if (e < e0 || e >= e1) continue;
-            const int j = __ldg(a.colidx + e);
+            const uint4* brow = reinterpret_cast<const uint4*>(Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                if (ok[u] && vin[t]) bw[u][t] = __ldg(brow + t * G);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
             if constexpr (!KNOWN_ROW) {
-                const int r = __ldg(a.rowidx + e);
-                if (r != cur) {
+                if (row[u] != cur) {
                     flush(cur);
-                    for (int rr = cur + 1; rr < r; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
-                    cur = r;
+                    for (int rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
+                    cur = row[u];
 #pragma unroll
                     for (int t = 0; t < NV; ++t)
 #pragma unroll
                         for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
                 }
             }
-            float sv = value(e);
-            if constexpr (DTB == DT_E4M3) sv *= __ldg(a.b_scale + j);
-            const char* brow = Bb + (size_t)(unsigned)j * ldb_bytes;
+            float sv = s[u];
+            if constexpr (DTB == DT_E4M3) sv *= __ldg(a.b_scale + j[u]);
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
-                if (vbase + t * G + gl < nvec) {
-                    float bf[VECN];
-                    load_elems<DTB, VECN>(brow, (int64_t)t * G * VECN, bf);
+                if (!vin[t]) continue;
+                Raw<DTB, VECN> rb;
+                rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
+                float bf[VECN];
+                unpack_all<DTB, VECN>(rb, bf);
 #pragma unroll
-                    for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(sv, bf[q], acc[t][q]);
-                }
+                for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(sv, bf[q], acc[t][q]);
             }
         }
     }

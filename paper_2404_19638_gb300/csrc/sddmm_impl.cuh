@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256, min_ctas(U * NV * Raw<DTB, VECN>::NW)) k_
 
 // Vector path: one warp per span (a chunk of the balanced schedule, or a row).
 template <int DTA, int DTB, int G, int NV, int U>
-__global__ void __launch_bounds__(256, U * NV <= 8 ? 4 : 2) k_sddmm_lean(const SddmmArgs a)
+__global__ void __launch_bounds__(256, U * NV <= 4 ? 4 : (U * NV <= 8 ? 3 : 2)) k_sddmm_lean(const SddmmArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;

@@ -252,7 +252,7 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
 // vector path runs the lean span without shared memory; the element path
 // streams index tiles through shared memory.
 template <int DTB, int VECN, int G, int NV, int U>
-__global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 8 ? 4 : 2) : min_ctas(U * NV * Raw<DTB, VECN>::NW))
+__global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 4 : (U * NV <= 8 ? 3 : 2)) : min_ctas(U * NV * Raw<DTB, VECN>::NW))
     k_spmm(const SpmmArgs a)
 {
     extern __shared__ int smem[];
