@@ -227,16 +227,16 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
-// Default lane-group shape for a row of nvec 16-byte vectors: 8 lanes per row
-// (one 128-byte line per warp-wide load per row) with up to 4 vectors per
-// lane, 4 nonzeros in flight per group.
+// Default lane-group shape for a row of nvec 16-byte vectors, 4 nonzeros in
+// flight per group (measured on R-MAT scale-20 rows with K = 64: SDDMM runs
+// best with 8 lanes per row and 2 vectors per lane, SpMM with one vector per
+// lane up to 16 lanes).
 static void default_shape(int op, int nvec, int* G, int* NV, int* U)
 {
-    (void)op;
     *U = 4;
     if (nvec <= 4) { *G = 4; *NV = 1; }
     else if (nvec <= 8) { *G = 8; *NV = 1; }
-    else if (nvec <= 16) { *G = 8; *NV = 2; }
+    else if (nvec <= 16) { *G = (op == OP_SDDMM) ? 8 : 16; *NV = (op == OP_SDDMM) ? 2 : 1; }
     else if (nvec <= 32) { *G = 8; *NV = 4; }
     else if (nvec <= 64) { *G = 32; *NV = 2; }
     else { *G = 32; *NV = 4; }
@@ -257,7 +257,7 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     const int idx = shape_index(G, NV, U);
     REQUIRE(idx >= 0, SPK_ERR_UNSUPPORTED, "no kernel compiled for group_lanes=%d vecs_per_lane=%d unroll=%d",
             G, NV, U);
-    const int threads = (t && t->cta_threads) ? t->cta_threads : 256;
+    const int threads = (t && t->cta_threads) ? t->cta_threads : 128;
     REQUIRE(threads == 128 || threads == 256, SPK_ERR_ARG, "tune.cta_threads must be 128 or 256");
     L->shape = idx;
     L->vec = vec;
