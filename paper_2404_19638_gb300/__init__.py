@@ -14,6 +14,7 @@ from .sparse import CSR, TransposePlan, DEFAULT_CHUNK_WORK
 from .ops import sddmm, spmm, spmm_t, cast, quantize_e4m3_rows
 from . import autograd
 from .batch import Batch, Item, OP_SDDMM, OP_SPMM
+from .autotune import Autotuner
 
 __all__ = ["CSR", "TransposePlan", "sddmm", "spmm", "spmm_t", "cast", "quantize_e4m3_rows", "autograd",
-           "Batch", "Item", "OP_SDDMM", "OP_SPMM", "SpkError", "Tune", "library_path", "DEFAULT_CHUNK_WORK"]
+           "Batch", "Item", "OP_SDDMM", "OP_SPMM", "Autotuner", "SpkError", "Tune", "library_path", "DEFAULT_CHUNK_WORK"]

@@ -120,9 +120,12 @@ class CSR:
             self._ws[K] = ws
         return ws
 
-    def transpose_plan(self, chunk_work: int = DEFAULT_CHUNK_WORK) -> "TransposePlan":
-        if self._tplan is None or self._tplan.chunk_work != chunk_work:
-            self._tplan = TransposePlan(self, chunk_work)
+    def transpose_plan(self, chunk_work: int | None = None) -> "TransposePlan":
+        """The transpose plan of S: the attached one when ``chunk_work`` is None
+        (built with the default chunk size on first use), else one of that
+        chunk size (rebuilt and attached if the attached one differs)."""
+        if self._tplan is None or (chunk_work is not None and self._tplan.chunk_work != chunk_work):
+            self._tplan = TransposePlan(self, DEFAULT_CHUNK_WORK if chunk_work is None else chunk_work)
         return self._tplan
 
     def tune_default(self, op: int, dtype_code: int, K: int) -> dict:
