@@ -147,6 +147,35 @@ spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
                     spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate,
                     void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
 
+/* Scratch held by the library for spk_spmm_static, in bytes (4 MiB): a
+ * file-scope device array that every GPU loading the library keeps until the
+ * process exits. */
+#define SPK_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* spk_spmm without a caller workspace: the same SpMM as spk_spmm.  The paper
+ * has no counterpart of this entry point.  It is for callers that cannot call cudaMalloc: code running inside a host
+ * that owns the device memory pool (a plugin with a memory budget fixed at
+ * load time, a framework whose caching allocator must see every buffer) or a
+ * loop where cudaMalloc's implicit device synchronisation is not allowed.
+ * The split-row carry slots go to the library's static scratch instead of a
+ * workspace; the caller still passes the inputs and C.  Neither the caller nor
+ * the library allocates: no cudaMalloc, cudaFree or allocating library call.
+ * Arguments, layouts and results are those of spk_spmm.
+ *  - Limit: spk_schedule_info's npieces x K x 4 must not exceed
+ *    SPK_STATIC_SCRATCH_BYTES; larger calls return SPK_ERR_WORKSPACE before
+ *    any launch (use spk_spmm then).
+ *  - Set-up: the first call on a device (the current one) looks up the
+ *    scratch's device address with cudaGetSymbolAddress; make that first call
+ *    before any stream capture.
+ *  - Sharing: every call on a device uses the same scratch, which keeps the
+ *    last call's contents.  Nothing in it needs to start at zero, so it is
+ *    never cleared.  Calls that overlap on the GPU (other streams, other host
+ *    threads) race on the scratch and give wrong results: order them. */
+spk_status spk_spmm_static(spk_csr S, const float* vals, const float* vals2,
+                           spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
+                           spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate,
+                           const spk_tune* tune, void* stream);
+
 /* ----------------------------------------------------- transpose plan -- */
 /* The CSC of S by a stable device radix sort on the column index: colptr[N+1],
  * rowidx[nnz] (rows ascending inside a column) and perm[nnz] (CSR slot of each

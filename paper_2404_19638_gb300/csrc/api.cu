@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -382,6 +383,63 @@ extern "C" spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
     REQUIRE(S, SPK_ERR_ARG, "spk_spmm: S is NULL");
     return spmm_common("spk_spmm", S, vals, vals2, dtb, B, ldb, b_scale, K, dtc, C, ldc, accumulate, workspace,
                        ws_bytes, tune, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// SpMM with library-held scratch
+// ----------------------------------------------------------------------------
+// Carry slots of spk_spmm_static.  A file-scope device array: every GPU that
+// loads the library holds SPK_STATIC_SCRATCH_BYTES of it until the process
+// exits.  In host code `g_static_scratch` is only a stand-in for the symbol;
+// its device address comes from cudaGetSymbolAddress, taken once per device
+// (with that device current) on the first spk_spmm_static call there.
+static __device__ __align__(256) float g_static_scratch[SPK_STATIC_SCRATCH_BYTES / sizeof(float)];
+
+static constexpr int kMaxStaticDevices = 64;
+static std::mutex g_static_mu;
+static void* g_static_addr[kMaxStaticDevices];
+
+static spk_status static_scratch_address(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: cudaGetDevice");
+    REQUIRE(dev >= 0 && dev < kMaxStaticDevices, SPK_ERR_UNSUPPORTED,
+            "spk_spmm_static: device ordinal %d is beyond the %d supported", dev, kMaxStaticDevices);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: cudaGetSymbolAddress");
+        REQUIRE(p && (reinterpret_cast<uintptr_t>(p) & 255u) == 0, SPK_ERR_CUDA,
+                "spk_spmm_static: scratch symbol address is NULL or misaligned");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_spmm_static(spk_csr S, const float* vals, const float* vals2, spk_dtype dtb,
+                                      const void* B, int64_t ldb, const float* b_scale, int32_t K, spk_dtype dtc,
+                                      void* C, int64_t ldc, int32_t accumulate, const spk_tune* tune,
+                                      void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_spmm_static: S is NULL");
+    REQUIRE(K >= 1, SPK_ERR_SHAPE, "spk_spmm_static: K must be >= 1 (got %d)", K);
+    const size_t need = S->has_sched ? (size_t)S->npieces * (size_t)K * 4 : 0;
+    REQUIRE(need <= (size_t)SPK_STATIC_SCRATCH_BYTES, SPK_ERR_WORKSPACE,
+            "spk_spmm_static: %lld split-row pieces x K = %d need %zu bytes of scratch, above the %zu bytes "
+            "held by the library (use spk_spmm with a caller workspace)",
+            (long long)S->npieces, K, need, (size_t)SPK_STATIC_SCRATCH_BYTES);
+    // No slot of the scratch has to start at zero: within one call every carry
+    // slot is written before it is read, so nothing is cleared.  (The arrival
+    // counters of split rows live in the schedule storage and the kernel
+    // returns them to zero.)
+    void* ws = nullptr;
+    spk_status st = static_scratch_address(&ws);
+    if (st != SPK_OK) return st;
+    return spmm_common("spk_spmm_static", S, vals, vals2, dtb, B, ldb, b_scale, K, dtc, C, ldc, accumulate, ws,
+                       (size_t)SPK_STATIC_SCRATCH_BYTES, tune, (cudaStream_t)stream);
 }
 
 // ----------------------------------------------------------------------------
