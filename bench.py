@@ -115,7 +115,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []                       # (host time of arrival, csv line)
+        self.window = None
 
     def __enter__(self):
         try:
@@ -124,13 +125,21 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0:     # sampler running before timing
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t_start: float, t_end: float) -> None:
+        """Host-clock bounds of the timed region; samples outside are ignored
+        (plus one sample after the end, which covers its last interval)."""
+        self.window = (t_start, t_end)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -142,7 +151,15 @@ class ClockSampler:
 
     def summary(self):
         rows = []
-        for ln in self.lines:
+        lines = self.lines
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [ln for t, ln in lines if t0 <= t <= t1]
+            after = [ln for t, ln in lines if t > t1][:1]
+            lines = inside + after
+        else:
+            lines = [ln for _, ln in lines]
+        for ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 9:
                 continue
@@ -256,11 +273,11 @@ def main(args):
     torch.cuda.synchronize(dev)
 
     events = []
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    wall0 = time.perf_counter()
     with ClockSampler(dev.index if world == 1 else local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        wall0 = time.perf_counter()
         for _ in range(args.steps):
             flush.zero_()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -269,6 +286,8 @@ def main(args):
             ev[2].record(stream)
             events.append(ev)
         torch.cuda.synchronize(dev)
+        clk.mark(wall0, time.perf_counter())
+        time.sleep(0.15)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -376,7 +395,7 @@ def main(args):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn"])
