@@ -68,11 +68,14 @@ typedef enum spk_dtype {
 /* Kernel choice.  Zero fields mean "library default".  See spk_tune_default. */
 typedef struct spk_tune {
     int32_t variant;        /* 0 default, 1 row-split (one lane group per row),
-                               2 balanced chunks (merge-path schedule, needs spk_schedule_build) */
+                               2 balanced chunks (merge-path schedule, needs spk_schedule_build),
+                                 gathered rows staged in shared memory where the path supports it,
+                               3 balanced chunks, gathered rows held in registers */
     int32_t group_lanes;    /* lanes that share one row of the dense factor: 4, 8, 16, 32 */
     int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
     int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
-    int32_t cta_threads;    /* threads per CTA: 128, 256, 512                      */
+    int32_t cta_threads;    /* threads per CTA: 128 or 256 (register paths)        */
+    int32_t stages;         /* batch slots of a shared-memory ring: 2 or 4         */
 } spk_tune;
 
 typedef struct spk_csr_s* spk_csr;       /* pattern of S (+ its schedule)      */

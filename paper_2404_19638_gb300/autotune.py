@@ -141,8 +141,11 @@ class Autotuner:
         for W in self.chunk_works:
             self._attach(S, op, W)
             for (G, NV, U) in candidate_shapes(K, dtype):
-                for thr in self.threads:
-                    t = {"variant": 2, "group_lanes": G, "vecs_per_lane": NV, "unroll": U, "cta_threads": thr}
+                # shared-memory ring (2 or 4 slots), then the register path at each CTA size
+                cands = [{"variant": 2, "stages": st} for st in (2, 4)]
+                cands += [{"variant": 3, "cta_threads": thr} for thr in self.threads]
+                for c in cands:
+                    t = {"group_lanes": G, "vecs_per_lane": NV, "unroll": U, **c}
                     try:
                         ms = self._time(lambda: run(t))
                     except SpkError:

@@ -32,7 +32,7 @@ class SpkError(RuntimeError):
 class Tune(ctypes.Structure):
     """spk_tune: 0 fields mean the library default."""
     _fields_ = [("variant", _i32), ("group_lanes", _i32), ("vecs_per_lane", _i32), ("unroll", _i32),
-                ("cta_threads", _i32)]
+                ("cta_threads", _i32), ("stages", _i32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -246,7 +246,7 @@ static void default_shape(int op, int nvec, int* G, int* NV, int* U)
 static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, const spk_tune* t, Launch* L)
 {
     const int variant = (t && t->variant) ? t->variant : (S->has_sched ? 2 : 1);
-    REQUIRE(variant == 1 || variant == 2, SPK_ERR_ARG, "tune.variant %d is not 0, 1 or 2", variant);
+    REQUIRE(variant >= 1 && variant <= 3, SPK_ERR_ARG, "tune.variant %d is not 0, 1, 2 or 3", variant);
     REQUIRE(variant == 1 || S->has_sched, SPK_ERR_STATE, "balanced variant needs spk_schedule_build first");
     const int vecn = vec ? vec_elems(dtb) : 1;
     const int nvec = K / vecn;
@@ -263,7 +263,11 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     L->shape = idx;
     L->vec = vec;
     L->threads = threads;
-    L->chunks = (variant == 2);
+    L->chunks = (variant >= 2);
+    L->ring = (variant == 2);
+    const int stages = (t && t->stages) ? t->stages : 2;
+    REQUIRE(stages == 2 || stages == 4, SPK_ERR_ARG, "tune.stages must be 2 or 4");
+    L->stages = stages;
     return SPK_OK;
 }
 
@@ -277,11 +281,12 @@ extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int3
     spk_status st = resolve(P, op, dt, K, vec, nullptr, &L);
     if (st != SPK_OK) return st;
     const Shape sh = shape_at(L.shape);
-    out->variant = L.chunks ? 2 : 1;
+    out->variant = L.chunks ? (L.ring ? 2 : 3) : 1;
     out->group_lanes = sh.G;
     out->vecs_per_lane = sh.NV;
     out->unroll = sh.U;
     out->cta_threads = L.threads;
+    out->stages = L.stages;
     return SPK_OK;
 }
 

@@ -90,6 +90,35 @@ __device__ __forceinline__ void load_elems(const void* base, int64_t idx, float*
     }
 }
 
+// Dot-product accumulation in element pairs: acc.x collects the even
+// elements, acc.y the odd ones, one packed FMA (two IEEE fused multiply-adds,
+// round to nearest) per pair; the caller adds acc.x + acc.y once per dot.
+template <int N>
+__device__ __forceinline__ void dot_pairs(float2& acc, const float* a, const float* b)
+{
+    static_assert(N % 2 == 0, "pairs");
+#pragma unroll
+    for (int q = 0; q < N; q += 2) acc = __ffma2_rn(make_float2(a[q], a[q + 1]), make_float2(b[q], b[q + 1]), acc);
+}
+
+// acc[q] += s * b[q] for N elements (pairs through the packed FMA; the result
+// of every element is the same as one fmaf).
+template <int N>
+__device__ __forceinline__ void axpy_pairs(float* acc, float s, const float* b)
+{
+    if constexpr (N % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < N; q += 2) {
+            const float2 r = __ffma2_rn(make_float2(s, s), make_float2(b[q], b[q + 1]), make_float2(acc[q], acc[q + 1]));
+            acc[q] = r.x;
+            acc[q + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = fmaf(s, b[q], acc[q]);
+    }
+}
+
 // Raw (still packed) elements: gathered rows stay packed in registers while
 // their loads are in flight and are widened at the FMA, so a 16-byte vector
 // costs 4 registers whatever the dtype.
@@ -305,6 +334,8 @@ struct Launch {
     bool vec;          // 16-byte vector mode (else one element per lane slot)
     int threads;
     bool chunks;       // balanced schedule
+    bool ring;         // stage gathered rows in a shared-memory ring where the path has one
+    int stages;        // batch slots of the ring (2 or 4)
 };
 
 // Launchers (one per dtype family; defined in the sddmm_*.cu / spmm_*.cu files).

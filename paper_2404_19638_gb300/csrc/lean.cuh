@@ -121,6 +121,7 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
             p[u] = 0.f;
             if (!ok[u]) continue;
             if (row[u] != cur) { cur = row[u]; load_a(cur); }
+            float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < NV; ++t) {
                 if (!vin[t]) continue;
@@ -128,9 +129,9 @@ __device__ __forceinline__ void sddmm_warp_span(const SddmmArgs& a, int lane, in
                 rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
                 float bf[VECN];
                 unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                for (int q = 0; q < VECN; ++q) p[u] = fmaf(av[t][q], bf[q], p[u]);
+                dot_pairs<VECN>(acc, av[t], bf);
             }
+            p[u] = acc.x + acc.y;
             if constexpr (DTA == DT_E4M3) p[u] *= __ldg(a.a_scale + cur) * __ldg(a.b_scale + j[u]);
         }
         // Reduce-scatter over the low log2(U) lane bits, then butterflies over
@@ -277,8 +278,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
                 rb.w[0] = bw[u][t].x; rb.w[1] = bw[u][t].y; rb.w[2] = bw[u][t].z; rb.w[3] = bw[u][t].w;
                 float bf[VECN];
                 unpack_all<DTB, VECN>(rb, bf);
-#pragma unroll
-                for (int q = 0; q < VECN; ++q) acc[t][q] = fmaf(sv, bf[q], acc[t][q]);
+                axpy_pairs<VECN>(acc[t], sv, bf);
             }
         }
     }

@@ -17,7 +17,7 @@
 // long rows are cut into pieces; SDDMM outputs are per nonzero, so pieces
 // need no combining.
 #pragma once
-#include "lean.cuh"
+#include "ring.cuh"
 
 namespace spk {
 
@@ -185,6 +185,36 @@ __global__ void __launch_bounds__(256, U * NV <= 4 ? 4 : (U * NV <= 8 ? 3 : 2)) 
     }
 }
 
+// Ring path: one warp per span of the balanced schedule, gathered rows staged
+// in the warp's shared-memory ring of D batch slots (ring.cuh).
+template <int DT, int G, int NV, int U, int D>
+__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(sddmm_ring_bytes(G, NV, U, D)))
+    k_sddmm_ring(const SddmmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wsm = ring_smem + (threadIdx.x >> 5) * sddmm_ring_bytes(G, NV, U, D);
+    const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const bool allv = a.K / vec_elems(DT) >= G * NV;
+    for (int64_t c = wid; c < a.nchunks; c += nwarps) {
+        const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+        if (allv) sddmm_ring_span<DT, G, NV, U, D, true>(a, lane, wsm, b0.y, b1.y);
+        else sddmm_ring_span<DT, G, NV, U, D, false>(a, lane, wsm, b0.y, b1.y);
+    }
+}
+
+template <int DT, int D>
+inline const void* sddmm_ring_kernel_for(int shape)
+{
+    switch (shape) {
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_sddmm_ring<DT, G_, NV_, U_, D>;
+        SPK_SHAPES(X)
+#undef X
+    }
+    return nullptr;
+}
+
 template <int DTA, int DTB, int VECN>
 inline const void* sddmm_kernel_for(int shape)
 {
@@ -214,6 +244,23 @@ cudaError_t launch_sddmm_t(const Launch& L, const SddmmArgs& a, cudaStream_t s)
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
     const bool lean = L.vec && (a.K / vec_elems(DTB)) <= sh.G * sh.NV;
+    if constexpr (DTA == DTB && DTB != DT_E4M3) {
+        if (lean && L.ring && a.bnd) {
+            const void* rf = L.stages == 4 ? sddmm_ring_kernel_for<DTB, 4>(L.shape)
+                                           : sddmm_ring_kernel_for<DTB, 2>(L.shape);
+            if (!rf) return cudaErrorInvalidValue;
+            const int warps = RING_THREADS / 32;
+            int64_t blocks = (items + warps - 1) / warps;
+            if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+            const size_t smem = (size_t)warps * sddmm_ring_bytes(sh.G, sh.NV, sh.U, L.stages == 4 ? 4 : 2);
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(rf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            void* args[] = {(void*)&a};
+            return cudaLaunchKernel(rf, dim3((unsigned)blocks), dim3(RING_THREADS), args, smem, s);
+        }
+    }
     const void* fn = lean ? sddmm_lean_kernel_for<DTA, DTB>(L.shape)
                           : (L.vec ? sddmm_kernel_for<DTA, DTB, vec_elems(DTB)>(L.shape)
                                    : sddmm_kernel_for<DTA, DTB, 1>(L.shape));

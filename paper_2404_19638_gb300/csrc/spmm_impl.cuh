@@ -16,7 +16,7 @@
 // adds the pieces in chunk order and writes the row.  The sum order is fixed
 // by the schedule, so results are bitwise reproducible.
 #pragma once
-#include "lean.cuh"
+#include "ring.cuh"
 
 namespace spk {
 
@@ -236,8 +236,7 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
                 for (int t2 = 0; t2 < NV; ++t2) {
                     float bf[VECN];
                     unpack_all<DTB, VECN>(bw[u][t2], bf);
-#pragma unroll
-                    for (int q = 0; q < VECN; ++q) acc[t2][q] = fmaf(s[u], bf[q], acc[t2][q]);
+                    axpy_pairs<VECN>(acc[t2], s[u], bf);
                 }
             }
         }
@@ -284,6 +283,39 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 4 : (U * NV <= 
     }
 }
 
+// Ring path: one group per span of the balanced schedule, gathered rows
+// staged in the warp's shared-memory ring (ring.cuh).
+template <int DT, int G, int NV, int U>
+__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(NV, U))) k_spmm_ring(const SpmmArgs a)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    const Group<G> g;
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (spmm_ring_bytes(NV, U) / 16);
+    const int kb = blockIdx.y, nkb = gridDim.y;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool allv = a.K / vec_elems(DT) >= (kb + 1) * G * NV;
+    for (int64_t c = gid; c < a.nchunks; c += ngroups) {
+        const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+        const int4 m = a.meta[c];
+        if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
+        const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
+        if (allv) spmm_ring_span<DT, G, NV, U, true>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+        else spmm_ring_span<DT, G, NV, U, false>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    }
+}
+
+template <int DT>
+inline const void* spmm_ring_kernel_for(int shape)
+{
+    switch (shape) {
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm_ring<DT, G_, NV_, U_>;
+        SPK_SHAPES(X)
+#undef X
+    }
+    return nullptr;
+}
+
 template <int DTB, int VECN>
 inline const void* spmm_kernel_for(int shape)
 {
@@ -306,6 +338,24 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     const int nkb = (nvec + sh.G * sh.NV - 1) / (sh.G * sh.NV);
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
+    if constexpr (DTB != DT_E4M3) {
+        const bool ring_ok = L.vec && L.ring && a.bnd && !a.vperm && !a.vals2 && (!a.vals || a.vals_staged);
+        if (ring_ok) {
+            const void* rf = spmm_ring_kernel_for<DTB>(L.shape);
+            if (!rf) return cudaErrorInvalidValue;
+            const int64_t groups_per_cta = RING_THREADS / sh.G;
+            int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
+            if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+            if (nkb > 65535) return cudaErrorInvalidValue;
+            const size_t smem = (size_t)(RING_THREADS / 32) * spmm_ring_bytes(sh.NV, sh.U);
+            if (smem > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(rf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            void* args[] = {(void*)&a};
+            return cudaLaunchKernel(rf, dim3((unsigned)blocks, (unsigned)nkb), dim3(RING_THREADS), args, smem, s);
+        }
+    }
     const int64_t groups_per_cta = L.threads / sh.G;
     int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;

@@ -93,7 +93,7 @@ def spmm(S: CSR, B: torch.Tensor, vals=None, vals2=None, *, b_scale=None, out: t
     vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
     b_scale = _scale(b_scale, S.N, "b_scale", S.device)
     t = Tune.make(tune)
-    ws = S.workspace(K) if (S.has_schedule and (t is None or t.variant in (0, 2))) else None
+    ws = S.workspace(K) if (S.has_schedule and (t is None or t.variant != 1)) else None
     check(lib().spk_spmm(S.handle, _ptr(vals), _ptr(vals2), dtb, B.data_ptr(), ldb, _ptr(b_scale), K, dtc,
                          out.data_ptr(), ldc, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
                          None if t is None else ctypes.byref(t), _stream(S.device)), "spk_spmm")
@@ -121,7 +121,7 @@ def spmm_t(S: CSR, Y: torch.Tensor, vals=None, vals2=None, *, y_scale=None, out:
     vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
     y_scale = _scale(y_scale, S.M, "y_scale", S.device)
     t = Tune.make(tune)
-    ws = P.workspace(K) if (t is None or t.variant in (0, 2)) else None
+    ws = P.workspace(K) if (t is None or t.variant != 1) else None
     check(lib().spk_spmm_t(P.handle, _ptr(vals), _ptr(vals2), dty, Y.data_ptr(), ldy, _ptr(y_scale), K, dtx,
                            out.data_ptr(), ldx, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
                            None if t is None else ctypes.byref(t), _stream(S.device)), "spk_spmm_t")

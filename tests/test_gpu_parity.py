@@ -36,13 +36,13 @@ SHAPES = [(4, 1, 4), (8, 1, 8), (16, 1, 8), (32, 1, 8), (8, 2, 8), (16, 2, 8), (
 
 
 @pytest.mark.parametrize("K", [1, 3, 8, 24, 32, 40, 64, 128, 136])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_sddmm_spmm_f32_k_sweep(spk, K, variant):
     M, N = 700, 500
     rp, ci, vals, A, B = _case(M, N, K, seed=K, long_row=3000)
     S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV, chunk_work=128)
     tA, tB = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
-    tune = {"variant": variant}
+    tune = {"variant": variant} if variant < 4 else {"variant": 2, "stages": 4}
     out = spk.sddmm(S, tA, tB, tune=tune).cpu().numpy()
     C = spk.spmm(S, tB, tune=tune).cpu().numpy()
     X = spk.spmm_t(S, tA, tune=tune).cpu().numpy()
@@ -59,12 +59,17 @@ def test_all_compiled_shapes(spk, shape, K):
     S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV, chunk_work=96)
     tA, tB = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
     G, NV, U = shape
-    for variant in (1, 2):
-        tune = {"variant": variant, "group_lanes": G, "vecs_per_lane": NV, "unroll": U}
+    got = {}
+    for variant, stages in ((1, 0), (2, 2), (2, 4), (3, 0)):
+        tune = {"variant": variant, "group_lanes": G, "vecs_per_lane": NV, "unroll": U, "stages": stages}
         out = spk.sddmm(S, tA, tB, tune=tune).cpu().numpy()
         C = spk.spmm(S, tB, tune=tune).cpu().numpy()
         assert comp_err(out, oracle.sddmm(rp, ci, A, B, vals), oracle.sddmm(rp, ci, A, B, vals, absmode=True)) <= TOL
         assert comp_err(C, oracle.spmm(rp, ci, B, vals), oracle.spmm(rp, ci, B, vals, absmode=True)) <= TOL
+        got[(variant, stages)] = (out, C)
+    # shared-memory staging changes where gathered rows wait, not the arithmetic
+    for k in ((2, 4), (3, 0)):
+        assert np.array_equal(got[(2, 2)][0], got[k][0]) and np.array_equal(got[(2, 2)][1], got[k][1])
 
 
 @pytest.mark.parametrize("W", [32, 64, 512, 4096])
@@ -195,7 +200,7 @@ def test_integer_inputs_bitwise(spk, dt):
     B = g.integers(-3, 4, (N, K)).astype(np.float32)
     S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV, chunk_work=64)
     tA, tB = torch.from_numpy(A).to(DEV).to(dt), torch.from_numpy(B).to(DEV).to(dt)
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         out = spk.sddmm(S, tA, tB, tune={"variant": variant}).cpu().numpy()
         C = spk.spmm(S, tB, tune={"variant": variant}).cpu().numpy()
         X = spk.spmm_t(S, tA, tune={"variant": variant}).cpu().numpy()
