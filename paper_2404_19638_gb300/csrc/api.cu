@@ -232,12 +232,20 @@ enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 // flight per group (measured on R-MAT scale-20 rows with K = 64: SDDMM runs
 // best with 8 lanes per row and 2 vectors per lane, SpMM with one vector per
 // lane up to 16 lanes).
+// Defaults from shape sweeps on GB300 (R-MAT scale 20, K = 64): SDDMM
+// favours 4-lane groups with two vectors at 8 vectors a row and 8-lane groups
+// at 16; SpMM favours one vector a lane (16 lanes, 8 nonzeros in flight at
+// 16 vectors).
 static void default_shape(int op, int nvec, int* G, int* NV, int* U)
 {
     *U = 4;
     if (nvec <= 4) { *G = 4; *NV = 1; }
-    else if (nvec <= 8) { *G = 8; *NV = 1; }
-    else if (nvec <= 16) { *G = (op == OP_SDDMM) ? 8 : 16; *NV = (op == OP_SDDMM) ? 2 : 1; }
+    else if (nvec <= 8) { *G = (op == OP_SDDMM) ? 4 : 8; *NV = (op == OP_SDDMM) ? 2 : 1; }
+    else if (nvec <= 16) {
+        *G = (op == OP_SDDMM) ? 8 : 16;
+        *NV = (op == OP_SDDMM) ? 2 : 1;
+        *U = (op == OP_SDDMM) ? 4 : 8;
+    }
     else if (nvec <= 32) { *G = 8; *NV = 4; }
     else if (nvec <= 64) { *G = 32; *NV = 2; }
     else { *G = 32; *NV = 4; }
