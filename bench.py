@@ -195,10 +195,45 @@ def time_oracle_step(P, rows):
     return time.perf_counter() - t0
 
 
+def reference_arm_batch(args):
+    """Reference arm of the batched workload: the oracle on a bounded sample
+    (every 16th matrix from an offset that moves each step, about 2000 rows
+    of each), one host core."""
+    import oracle
+    oracle.build()
+    probs = synth.batch(seed=0)
+    times, flops = [], []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        fl = 0.0
+        for p in probs[s % 16::16]:
+            rows = np.arange(0, p.M, max(1, p.M // 2000), dtype=np.int64)
+            nz = int(np.diff(p.rowptr.astype(np.int64))[rows].sum())
+            oracle.sddmm(p.rowptr, p.colidx, p.A, p.B, p.vals, rows=rows)
+            oracle.spmm(p.rowptr, p.colidx, p.B, p.vals, rows=rows)
+            fl += 4.0 * nz * p.K
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            flops.append(fl)
+    T = sum(times)
+    value = sum(flops) / T / 1e9
+    sample = "per step: every 16th matrix (offset = step mod 16), about 2000 evenly spaced rows each, FP64 oracle, single thread"
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": BATCH_DESC}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload == "batch":
+        return reference_arm_batch(args)
     P, desc = load_workload(args.workload)
     import oracle
     oracle.build()
@@ -228,9 +263,68 @@ def reference_arm(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def event_ms(fn, stream, flush, reps=5):
+    """Median CUDA-event time of fn on `stream`, L2 flushed before each rep."""
+    import torch
+    fn()
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def aux_measurements(spk, S, P, A32, A, dt, elt, flush, stream, args):
+    """The other steps of the path on the same pattern, outside the timed step:
+    setup (schedule, transpose plan; wall clock, includes their host work),
+    S^T Y through the plan, and the precision conversions."""
+    import torch
+    dev = A32.device
+
+    def wall_ms(fn, reps=3):
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize(dev)
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts)
+
+    S2 = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), device=dev, schedule=False)
+    out = {"schedule_build_ms": wall_ms(lambda: S2.build_schedule(args.chunk_work)),
+           "transpose_plan_build_ms": wall_ms(lambda: spk.TransposePlan(S, args.chunk_work))}
+    del S2
+    plan = S.transpose_plan(args.chunk_work)
+    X = torch.empty((P.N, P.K), dtype=torch.float32, device=dev)
+    t = event_ms(lambda: spk.spmm_t(S, A, out=X, plan=plan), stream, flush)
+    # colptr, CSC rows, COO rows of S^T, slot permutation, permuted values; Y once, X written once
+    bytes_t = 4 * (P.N + 1) + 16 * P.nnz + P.M * P.K * elt + P.N * P.K * 4
+    out["spmm_t_ms"] = t
+    out["spmm_t_algo_gbs"] = bytes_t / (t / 1e3) / 1e9
+    n = A32.numel()
+    t = event_ms(lambda: spk.cast(A32, torch.bfloat16), stream, flush)
+    out["cast_bf16_ms"] = t
+    out["cast_bf16_algo_gbs"] = 6 * n / (t / 1e3) / 1e9
+    t = event_ms(lambda: spk.quantize_e4m3_rows(A32), stream, flush)
+    out["quantize_e4m3_ms"] = t
+    out["quantize_e4m3_algo_gbs"] = (5 * n + 4 * A32.size(0)) / (t / 1e3) / 1e9
+    out["note"] = ("measured after the timed step on the same pattern; builds by wall clock, "
+                   "kernels by CUDA events with the L2 flushed")
+    return out
+
+
 def main(args):
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch":
+        return main_batch(args)
 
     import torch
     import torch.distributed as dist
@@ -347,6 +441,8 @@ def main(args):
             dist.destroy_process_group()
         return 0
 
+    aux = None if args.no_aux else aux_measurements(spk, S, P, A32, A, dt, elt, flush, stream, args)
+
     pk, pk_kind = peaks()
     ab = algorithmic_bytes(P, elt)
     ms_sd, ms_sp = statistics.mean(t_sd), statistics.mean(t_sp)
@@ -375,6 +471,8 @@ def main(args):
         "gpu_launches": 2 * args.steps,
         "wall_s": wall,
     }
+    if aux is not None:
+        line["aux"] = aux
     summ = clk.summary()
     line["clocks"] = summ
     if world == 1 and not args.no_cpu_baseline:
@@ -392,13 +490,173 @@ def main(args):
     return 0
 
 
+BATCH_DESC = ("batch: 256 independent matrices, n log-uniform in [1e3, 2e5] (9,570,975 rows, 147,971,228 nonzeros); "
+              "128 Erdos-Renyi with exactly d ~ U{4..32} columns per row, 128 R-MAT edge factor 16; K ~ U{16,32,64}; "
+              "values, A, B U[-1,1]; every matrix runs SDDMM and SpMM")
+
+
+def main_batch(args):
+    """The batched work list: SDDMM and SpMM of all 256 matrices (512 work
+    items) in one persistent launch, replayed from a CUDA graph each step."""
+    import torch
+    import torch.distributed as dist
+    import paper_2404_19638_gb300 as spk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dt = torch.float32 if args.dtype == "f32" else torch.bfloat16
+    elt = 4 if args.dtype == "f32" else 2
+    probs = synth.batch(seed=0)
+    items, keep = [], []
+    flops_step, algo = 0.0, 0
+    h2d = d2h = 0
+    for p in probs:
+        S = spk.CSR(p.rowptr, p.colidx, (p.M, p.N), torch.from_numpy(p.vals), device=dev, chunk_work=args.chunk_work)
+        A = torch.from_numpy(p.A).to(dev).to(dt)
+        B = torch.from_numpy(p.B).to(dev).to(dt)
+        out = torch.empty(p.nnz, dtype=torch.float32, device=dev)
+        C = torch.empty((p.M, p.K), dtype=torch.float32, device=dev)
+        items.append(spk.Item(spk.OP_SDDMM, S, B, out, A=A))
+        items.append(spk.Item(spk.OP_SPMM, S, B, C))
+        keep.append((S, A, B, out, C, p))
+        flops_step += 2.0 * 2.0 * p.nnz * p.K
+        ab = algorithmic_bytes(p, elt)
+        algo += ab["sddmm"] + ab["spmm"]
+        h2d += p.A.nbytes + p.B.nbytes + p.vals.nbytes
+        d2h += out.numel() * 4 + C.numel() * 4
+    batch = spk.Batch(items)
+    batch.capture()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        flush.zero_()
+        batch.replay()
+    torch.cuda.synchronize(dev)
+    events = []
+    with ClockSampler(dev.index if world == 1 else local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.replay()
+            e1.record(stream)
+            events.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        clk.mark(wall0, time.perf_counter())
+        time.sleep(0.15)
+    if world > 1:
+        dist.barrier()
+    T = sum(a.elapsed_time(b) for a, b in events) / 1e3
+    if world > 1:
+        tt = torch.tensor([T], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        T = float(tt.item())
+    ms = 1e3 * T / args.steps
+
+    # the same work as one launch per (matrix, op), for comparison
+    def per_matrix():
+        for S, A, B, out, C, p in keep:
+            spk.sddmm(S, A, B, out=out)
+            spk.spmm(S, B, out=C)
+    per_ms = event_ms(per_matrix, stream, flush, reps=3)
+
+    # end to end: inputs from pinned host memory, outputs back, one persistent launch
+    hosts = [(torch.from_numpy(p.A).pin_memory(), torch.from_numpy(p.B).pin_memory(),
+              torch.from_numpy(p.vals).pin_memory(), torch.empty(p.nnz).pin_memory(),
+              torch.empty((p.M, p.K)).pin_memory()) for (_, _, _, _, _, p) in keep]
+    stage = [(torch.empty(p.A.shape, device=dev), torch.empty(p.B.shape, device=dev)) for (_, _, _, _, _, p) in keep]
+
+    def e2e_step():
+        for (S, A, B, out, C, p), (hA, hB, hv, ho, hC), (sA, sB) in zip(keep, hosts, stage):
+            if dt == torch.float32:
+                A.copy_(hA, non_blocking=True)
+                B.copy_(hB, non_blocking=True)
+            else:
+                sA.copy_(hA, non_blocking=True)
+                sB.copy_(hB, non_blocking=True)
+                A.copy_(spk.cast(sA, dt))
+                B.copy_(spk.cast(sB, dt))
+            S.vals.copy_(hv, non_blocking=True)
+        batch.replay()
+        for (S, A, B, out, C, p), (hA, hB, hv, ho, hC), _ in zip(keep, hosts, stage):
+            ho.copy_(out, non_blocking=True)
+            hC.copy_(C, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_steps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    Te = e0.elapsed_time(e1) / 1e3
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    pk, pk_kind = peaks()
+    achieved = algo / (ms / 1e3) / 1e9
+    info = batch.info()
+    line = {
+        "metric": METRIC, "value": world * flops_step * args.steps / T / 1e9, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "matrices": len(keep), "work_items": len(items),
+                   "nnz": int(sum(p.nnz for *_, p in keep)), "rows": int(sum(p.M for *_, p in keep)),
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "launch": "one persistent kernel per step, replayed from a CUDA graph",
+                   "chunk_work": args.chunk_work, "parallelism": "replicas" if world > 1 else "single GPU"},
+        "kernels": {"batch_ms": ms, "per_matrix_launches_ms": per_ms, "per_matrix_launches": 2 * len(keep),
+                    "work_units": info["work_units"], "ctas": info["ctas"]},
+        "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "peak_kind": pk_kind, "algorithmic_bytes": algo,
+                     "traffic": None},
+        "e2e": {"value": world * flops_step * e2e_steps / Te / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        fl = 0.0
+        used = 0
+        for S, A, B, out, C, p in keep[::16]:
+            rows = np.arange(0, p.M, max(1, p.M // 2000), dtype=np.int64)
+            nz = int(np.diff(p.rowptr.astype(np.int64))[rows].sum())
+            oracle.sddmm(p.rowptr, p.colidx, p.A, p.B, p.vals, rows=rows)
+            oracle.spmm(p.rowptr, p.colidx, p.B, p.vals, rows=rows)
+            fl += 4.0 * nz * p.K
+            used += 1
+        t = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": fl / t / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                                "sample": f"every 16th matrix ({used}), about 2000 evenly spaced rows each, "
+                                          f"SDDMM + SpMM in the FP64 oracle on one host core, {t:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn", "batch"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--chunk-work", type=int, default=512)
     ap.add_argument("--tune-sddmm", default=None, help='JSON spk_tune fields, e.g. {"group_lanes": 8}')
@@ -406,6 +664,7 @@ def parse():
     ap.add_argument("--cpu-nnz", type=int, default=2_000_000, help="nonzeros in the CPU-baseline sample")
     ap.add_argument("--ref-nnz", type=int, default=500_000, help="nonzeros per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-aux", action="store_true", help="skip the setup / SpMM^T / conversion measurements")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3

@@ -190,10 +190,15 @@ spk_status spk_tplan_build(spk_csr S, int32_t chunk_work, void* storage, size_t 
 spk_status spk_tplan_arrays(spk_tplan P, const int32_t** colptr, const int32_t** rowidx,
                             const int32_t** perm);
 spk_status spk_tplan_destroy(spk_tplan P);
+/* Bytes of workspace an S^T Y with K columns needs: the values in CSC slot
+ * order (nnz floats) and the carry rows of split rows of S^T. */
 spk_status spk_spmm_t_workspace_size(spk_tplan P, int32_t K, size_t* bytes);
 
 /* X (N x K) = S^T Y (Y: M x K), or += with accumulate = 1.  vals / vals2 are
- * indexed like S's colidx (CSR order) and gathered through perm. */
+ * indexed like S's colidx (CSR order); the call first writes their product in
+ * CSC slot order (gathered through perm) into the workspace (>=
+ * spk_spmm_t_workspace_size bytes, 256-byte aligned; NULL only when that size
+ * is 0), then runs the SpMM kernels on the transposed pattern. */
 spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* vals2,
                       spk_dtype dty, const void* Y, int64_t ldy, const float* y_scale, int32_t K,
                       spk_dtype dtx, void* X, int64_t ldx, int32_t accumulate,

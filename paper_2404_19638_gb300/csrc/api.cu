@@ -348,7 +348,8 @@ extern "C" spk_status spk_spmm_workspace_size(spk_csr S, int32_t K, size_t* byte
 static spk_status spmm_common(const char* name, const spk_csr_s* S, const float* vals, const float* vals2,
                               spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
                               spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate, void* ws, size_t ws_bytes,
-                              const spk_tune* tune, cudaStream_t stream)
+                              const spk_tune* tune, cudaStream_t stream, bool vals_in_slot_order = false,
+                              bool check_only = false)
 {
     REQUIRE(valid_dt(dtb), SPK_ERR_DTYPE, "%s: unknown input dtype", name);
     REQUIRE(dtc == SPK_F32 || dtc == SPK_BF16 || dtc == SPK_F16, SPK_ERR_DTYPE,
@@ -372,11 +373,13 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
                 ws ? ws_bytes : (size_t)0, need);
         REQUIRE(aligned16(ws), SPK_ERR_WORKSPACE, "%s: workspace must be 16-byte aligned", name);
     }
+    if (check_only) return SPK_OK;
     SpmmArgs a;
     a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = K;
-    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vperm = S->vperm;
+    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
+    a.vperm = vals_in_slot_order ? nullptr : S->vperm;
     a.vals = vals; a.vals2 = vals2;
-    a.vals_staged = (vals && !vals2 && !S->vperm && aligned16(vals)) ? 1 : 0;
+    a.vals_staged = (vals && !vals2 && !a.vperm && aligned16(vals)) ? 1 : 0;
     a.B = B; a.ldb = ldb; a.b_scale = b_scale;
     a.C = C; a.ldc = ldc; a.dtc = dtc; a.accumulate = accumulate;
     a.bnd = L.chunks ? S->bnd : nullptr;
@@ -520,10 +523,14 @@ extern "C" spk_status spk_tplan_destroy(spk_tplan P)
     return SPK_OK;
 }
 
+// Workspace of S^T Y: the values in CSC slot order (nnz floats, 256-byte
+// aligned block), then the carry rows of split rows of S^T.
+static size_t spmm_t_vals_bytes(const spk_tplan_s* P) { return ((size_t)P->St.nnz * 4 + 255) & ~(size_t)255; }
+
 extern "C" spk_status spk_spmm_t_workspace_size(spk_tplan P, int32_t K, size_t* bytes)
 {
     REQUIRE(P && bytes && K >= 1, SPK_ERR_ARG, "spk_spmm_t_workspace_size: bad argument");
-    *bytes = (size_t)P->St.npieces * (size_t)K * 4;
+    *bytes = spmm_t_vals_bytes(P) + (size_t)P->St.npieces * (size_t)K * 4;
     return SPK_OK;
 }
 
@@ -533,8 +540,30 @@ extern "C" spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* va
                                  void* stream)
 {
     REQUIRE(P, SPK_ERR_ARG, "spk_spmm_t: P is NULL");
-    return spmm_common("spk_spmm_t", &P->St, vals, vals2, dty, Y, ldy, y_scale, K, dtx, X, ldx, accumulate,
-                       workspace, ws_bytes, tune, (cudaStream_t)stream);
+    REQUIRE(K >= 1, SPK_ERR_SHAPE, "spk_spmm_t: K must be >= 1 (got %d)", K);
+    const size_t vb = spmm_t_vals_bytes(P);
+    const size_t need = vb + (size_t)P->St.npieces * (size_t)K * 4;
+    REQUIRE(need == 0 || (workspace && ws_bytes >= need), SPK_ERR_WORKSPACE,
+            "spk_spmm_t: workspace has %zu bytes, needs %zu", workspace ? ws_bytes : (size_t)0, need);
+    REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "spk_spmm_t: workspace must be 256-byte aligned");
+    if (!workspace) ws_bytes = 0;
+    REQUIRE(valid_dt(dty), SPK_ERR_DTYPE, "spk_spmm_t: unknown input dtype");
+    char* w = reinterpret_cast<char*>(workspace);
+    // every argument check of the SpMM on S^T runs before the value permutation
+    spk_status st = spmm_common("spk_spmm_t", &P->St, (vals || vals2) ? reinterpret_cast<const float*>(w) : nullptr,
+                                nullptr, dty, Y, ldy, y_scale, K, dtx, X, ldx, accumulate, w ? w + vb : nullptr,
+                                w ? ws_bytes - vb : 0, tune, (cudaStream_t)stream, true, true);
+    if (st != SPK_OK) return st;
+    const float* vt = nullptr;
+    if ((vals || vals2) && P->St.nnz > 0) {
+        float* out = reinterpret_cast<float*>(w);
+        cudaError_t e = launch_permute_vals(P->perm, vals, vals2, P->St.nnz, out, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_t value permutation");
+        vt = out;
+    }
+    return spmm_common("spk_spmm_t", &P->St, vt, nullptr, dty, Y, ldy, y_scale, K, dtx, X, ldx, accumulate,
+                       w ? w + vb : nullptr, w ? ws_bytes - vb : 0, tune, (cudaStream_t)stream, true);
 }
 
 // ----------------------------------------------------------------------------

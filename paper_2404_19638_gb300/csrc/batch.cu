@@ -1,5 +1,6 @@
 // Batched persistent launch: many independent SDDMM / SpMM problems of uneven
-// size in ONE kernel.  Each item is cut into work units (one warp's worth of
+// size in ONE kernel, each warp staging its gathers through a shared-memory
+// ring (ring.cuh).  Each item is cut into work units (one warp's worth of
 // balanced-schedule chunks, times the K blocks of an SpMM); a persistent grid
 // of one wave of CTAs pulls units off a device counter.  No warp ever waits on
 // another: split SpMM rows are finished by their last-arriving piece (see
@@ -39,20 +40,34 @@ static const Shape kBatchShapeList[kBatchShapes] = {
 #undef X
 };
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 128;
 
-// SDDMM: one chunk per warp (groups take interleaved batches of it).
+// Shared-memory ring of one warp: the largest ring of the batched shapes.
+__host__ __device__ constexpr int batch_ring_bytes()
+{
+    int m = 0;
+#define X(i, G_, NV_, U_)                                                           \
+    m = sddmm_ring_bytes(G_, NV_, U_, 2) > m ? sddmm_ring_bytes(G_, NV_, U_, 2) : m; \
+    m = spmm_ring_bytes(NV_, U_) > m ? spmm_ring_bytes(NV_, U_) : m;
+    SPK_BATCH_SHAPES(X)
+#undef X
+    return m;
+}
+
+// SDDMM: one chunk per warp (groups take interleaved batches of it), gathered
+// rows through the warp's ring (ring.cuh).
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit)
+__device__ __noinline__ void batch_sddmm_unit(const SddmmArgs& a, int64_t unit, unsigned char* wsm)
 {
     if (unit >= a.nchunks) return;
     const int2 b0 = a.bnd[unit], b1 = a.bnd[unit + 1];
-    sddmm_warp_span<DT, DT, G, NV, U, false>(a, threadIdx.x & 31, b0.x, b0.y, b1.y);
+    if (a.K / vec_elems(DT) >= G * NV) sddmm_ring_span<DT, G, NV, U, 2, true>(a, threadIdx.x & 31, wsm, b0.y, b1.y);
+    else sddmm_ring_span<DT, G, NV, U, 2, false>(a, threadIdx.x & 31, wsm, b0.y, b1.y);
 }
 
 // SpMM: one chunk per lane group, 32/G consecutive chunks per unit.
 template <int DT, int G, int NV, int U>
-__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb)
+__device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, int nkb, unsigned char* wsm)
 {
     const Group<G> g;
     const int kb = (int)(unit % nkb);
@@ -62,13 +77,19 @@ __device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, in
     const int4 m = a.meta[c];
     if (b1.y == b0.y && m.z < b0.x) return;
     const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-    spmm_group_span<DT, G, NV, U, false>(a, g, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    uint4* wring = reinterpret_cast<uint4*>(wsm);
+    if (a.K / vec_elems(DT) >= (kb + 1) * G * NV)
+        spmm_ring_span<DT, G, NV, U, true>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    else
+        spmm_ring_span<DT, G, NV, U, false>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
 }
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
-                                               const int64_t* __restrict__ unit_begin, int64_t total_units,
-                                               unsigned long long* counter, unsigned int* done)
+__global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
+                                                  const int64_t* __restrict__ unit_begin, int64_t total_units,
+                                                  unsigned long long* counter, unsigned int* done)
 {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    unsigned char* wsm = batch_smem + (threadIdx.x >> 5) * batch_ring_bytes();
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long u = 0;
@@ -86,16 +107,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchDesc* __rest
         if (d.op == 0) {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local); break;              \
-    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local); break;
+    case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local, wsm); break;         \
+    case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local, wsm); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
         } else {
             switch (cls) {
 #define X(i, G_, NV_, U_)                                                           \
-    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb); break;        \
-    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb); break;
+    case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb, wsm); break;   \
+    case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb, wsm); break;
                 SPK_BATCH_SHAPES(X)
 #undef X
             }
@@ -278,7 +299,8 @@ extern "C" spk_status spk_batch_create(const spk_batch_item* items, int32_t coun
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, 0);
+    const size_t smem = (size_t)(kBatchThreads / 32) * batch_ring_bytes();
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, smem);
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
     spk_batch_s* B = new (std::nothrow) spk_batch_s();
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_create: out of host memory");
@@ -297,8 +319,9 @@ extern "C" spk_status spk_batch_run(spk_batch B, void* stream)
 {
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_run: handle is NULL");
     if (B->total_units == 0) return SPK_OK;
-    k_batch<<<B->grid, kBatchThreads, 0, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin, B->total_units,
-                                                        B->d_counter, B->d_done);
+    const size_t smem = (size_t)(kBatchThreads / 32) * batch_ring_bytes();
+    k_batch<<<B->grid, kBatchThreads, smem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin,
+                                                                   B->total_units, B->d_counter, B->d_done);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_run: ") + cudaGetErrorString(e));
     return SPK_OK;

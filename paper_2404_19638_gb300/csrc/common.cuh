@@ -374,6 +374,8 @@ struct TplanLayout {
     SchedLayout sl;
 };
 TplanLayout tplan_layout(int64_t M, int64_t N, int64_t nnz, int32_t W);
+cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const float* vals2, int64_t nnz, float* out,
+                                cudaStream_t s);
 cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
                             char* storage, char* temp, const TplanLayout& L, cudaStream_t s);
 

@@ -138,6 +138,29 @@ __global__ void k_rows_of(const int32_t* rowptr, int64_t M, const int32_t* perm,
     rowidx[p] = (int32_t)lo;
 }
 
+// Values of S^T in CSC slot order: out[p] = vals[perm[p]] * vals2[perm[p]]
+// (absent factors are 1), the same single FP32 product the SpMM kernels form.
+__global__ void k_permute_vals(const int32_t* __restrict__ perm, const float* __restrict__ vals,
+                               const float* __restrict__ vals2, int64_t nnz, float* __restrict__ out)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = __ldg(perm + p);
+        float v = vals ? __ldg(vals + e) : 1.f;
+        if (vals2) v *= __ldg(vals2 + e);
+        out[p] = v;
+    }
+}
+
+cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const float* vals2, int64_t nnz, float* out,
+                                cudaStream_t s)
+{
+    if (nnz <= 0) return cudaSuccess;
+    int64_t blocks = (nnz + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_permute_vals<<<(unsigned)blocks, 256, 0, s>>>(perm, vals, vals2, nnz, out);
+    return cudaGetLastError();
+}
+
 cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
                             char* storage, char* temp, const TplanLayout& L, cudaStream_t s)
 {

@@ -121,7 +121,7 @@ def spmm_t(S: CSR, Y: torch.Tensor, vals=None, vals2=None, *, y_scale=None, out:
     vals, vals2 = _vals(vals, S, "vals"), _vals(vals2, S, "vals2")
     y_scale = _scale(y_scale, S.M, "y_scale", S.device)
     t = Tune.make(tune)
-    ws = P.workspace(K) if (t is None or t.variant != 1) else None
+    ws = P.workspace(K)
     check(lib().spk_spmm_t(P.handle, _ptr(vals), _ptr(vals2), dty, Y.data_ptr(), ldy, _ptr(y_scale), K, dtx,
                            out.data_ptr(), ldx, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
                            None if t is None else ctypes.byref(t), _stream(S.device)), "spk_spmm_t")
