@@ -93,10 +93,11 @@ __device__ __forceinline__ void ring_fetch(const int4& t, int src0, int (&v)[U])
 // dense operands (F32, BF16 or F16).  ALLV: every lane's NV vectors lie
 // inside K (no per-vector predicates).
 //
-// Rows are non-decreasing along a span, so a group's batch stays in the row
-// of its previous batch exactly when its last nonzero does.  Such a full
-// batch (most batches on power-law rows) takes the fast path: no A work and
-// no per-nonzero checks.  Any other batch (span edge or a new row) takes the
+// Rows are non-decreasing along a span, so a batch lies in one row exactly
+// when its first and last nonzeros do.  Such a full batch takes the fast
+// path: no per-nonzero checks, and if its row is not the row of the group's
+// previous batch, that row's A slice arrives through the ring with the batch.
+// Any other batch (span edge, or a row starting inside the batch) takes the
 // general path: the first new row's A slice arrives through the ring, a
 // second new row inside the same batch is read directly.
 // ----------------------------------------------------------------------------
@@ -153,7 +154,7 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
             const int d = b % D;
             const int eg = tb0 + b * WB + grp * U;
             uint4* sB = ringB + d * U * NV * 32 + lane;
-            const bool fast = (eg >= e0) && (eg + U <= e1) && (row[U - 1] == ilast);
+            const bool fast = (eg >= e0) && (eg + U <= e1) && (row[0] == row[U - 1]);
             if (fast) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -162,11 +163,19 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
                     for (int t2 = 0; t2 < NV; ++t2)
                         if (vin[t2]) cpa16(sB + (u * NV + t2) * 32, brow + t2 * G * 16);
                 }
+                const bool fresh = row[0] != ilast;          // the batch starts a new row
+                if (fresh) {
+                    const char* arow = Ab + (size_t)(unsigned)row[0] * lda_bytes;
+#pragma unroll
+                    for (int t2 = 0; t2 < NV; ++t2)
+                        if (vin[t2]) cpa16(ringA + (d * NV + t2) * 32 + lane, arow + t2 * G * 16);
+                }
+                ilast = row[0];
                 if (gl < U) {
                     if (vals) cpa4(mval + d * WB + slot_l, vals + eg + gl);
                     if (vals2) cpa4(mval2 + d * WB + slot_l, vals2 + eg + gl);
                 }
-                if (gl == 0) mmeta[d * GPW + grp] = 1;
+                if (gl == 0) mmeta[d * GPW + grp] = fresh ? 3 : 1;
             } else {
                 int m = 0, prev = ilast, myrow = row[0];
 #pragma unroll
@@ -226,6 +235,16 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
         const uint4* sB = ringB + d * U * NV * 32 + lane;
         float p[U];
         if (meta & 1) {
+            if (meta & 2) {                              // new row from nonzero 0 on: its A slice is in the ring
+#pragma unroll
+                for (int t = 0; t < NV; ++t)
+                    if (vin[t]) {
+                        const uint4 v = ringA[(d * NV + t) * 32 + lane];
+                        Raw<DT, VECN> ra;
+                        ra.w[0] = v.x; ra.w[1] = v.y; ra.w[2] = v.z; ra.w[3] = v.w;
+                        unpack_all<DT, VECN>(ra, av[t]);
+                    }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float2 acc = make_float2(0.f, 0.f);
