@@ -68,6 +68,9 @@ def lib():
                                       ctypes.c_int, _p, _i64, _p, _i64, _p, _p]
             L.oracle_spmm_t.argtypes = [_i64, _i64, _i64, _p, _p, _p, _p, ctypes.c_int,
                                         ctypes.c_int, _p, _i64, _p, _i64, _p, _p]
+            L.oracle_fusedmm.argtypes = [_i64, _i64, _i64, _i64, _p, _p, _p, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, _p, _i64, ctypes.c_int, _p, _i64,
+                                         _i64, _p, _p, _p, _p]
             L.oracle_transpose.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
             L.oracle_merge_path.argtypes = [_i64, _p, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
             _lib = L
@@ -212,6 +215,30 @@ def spmm_t(rowptr, colidx, N, Y, vals=None, vals2=None, cols=None, *, fmt_y=None
     if rc:
         raise ValueError(f"oracle_spmm_t: bad input ({rc})")
     return out
+
+
+def fusedmm(rowptr, colidx, A, B, vals=None, *, heads=1, scale=1.0, softmax=False, rows=None, fmt_a=None,
+            fmt_b=None, absmode=False, N=None):
+    """SDDMM cascaded into SpMM (Sec. 2), per head, optional row softmax.
+    Returns (Y float64 (len(rows) or M) x K, scores float64 heads x nnz (NaN
+    outside the rows computed), lse float64 (len(rows) or M) x heads)."""
+    rowptr = _c(rowptr, np.int32); colidx = _c(colidx, np.int32)
+    A, fa = _dense(A, fmt_a); B, fb = _dense(B, fmt_b)
+    M, K = A.shape
+    if B.shape[1] != K:
+        raise ValueError("A and B must have the same number of columns")
+    N = B.shape[0] if N is None else N
+    rows = _rows(rows)
+    count = M if rows is None else rows.size
+    Y = np.empty((count, K))
+    scores = np.full((heads, colidx.size), np.nan)
+    lse = np.empty((count, heads))
+    rc = lib().oracle_fusedmm(M, N, K, int(heads), _ptr(rowptr), _ptr(colidx), _ptr(_c(vals, np.float64)),
+                              float(scale), int(bool(softmax)), int(absmode), fa, _ptr(A), K, fb, _ptr(B), K,
+                              0 if rows is None else rows.size, _ptr(rows), _ptr(Y), _ptr(scores), _ptr(lse))
+    if rc:
+        raise ValueError(f"oracle_fusedmm: bad input ({rc})")
+    return Y, scores, lse
 
 
 def transpose(rowptr, colidx, N):

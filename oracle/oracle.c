@@ -12,6 +12,8 @@
  *   SpMM    a_i = sum_j s_ij * b_j                                   (Sec. 3.2, Eq. 2)
  *   SpMM^T  x_j = sum_i s_ij * y_i  (the adjoint pair of Sec. 3.2: each nonzero
  *           takes / outputs two dense vectors)
+ *   FusedMM y_i = sum_j w_ij * b_j with w = the SDDMM scores (Sec. 2: SDDMM
+ *           cascaded into SpMM), per head, optionally row-softmax weights
  * plus the bookkeeping the GPU path needs a reference for:
  *   - a stable counting-sort transpose (CSR -> CSC with slot permutation),
  *   - the merge-path split point of the (row ends, nonzeros) merge, by walking,
@@ -235,6 +237,77 @@ int oracle_spmm(int64_t M, int64_t N, int64_t K,
                 double t = s * elem(dtb, B, j * ldb + k, b_scale, j);
                 c[k] += abs_mode ? fabs(t) : t;
             }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* FusedMM: the SDDMM -> SpMM cascade (Sec. 2) on the operands of Eq. 1 and   */
+/* Eq. 2, per head h of H equal slices of K (width D = K / H):                */
+/*   e_h(i,j) = scale * s_ij * sum_{k in head h} A[i,k] * B[j,k]              */
+/*   w_h(i,j) = e_h(i,j), or with row_softmax                                 */
+/*            = exp(e_h(i,j) - m) / sum_{j' in row i} exp(e_h(i,j') - m),     */
+/*              m = max_{j' in row i} e_h(i,j')                               */
+/*   Y[q, head h] = sum_{j in row i} w_h(i,j) * B[j, head h],   i = rows[q]   */
+/* abs_mode: the condition denominator of Y: |w| |B| summed, where a plain    */
+/* weight is replaced by |scale s_ij| sum_k |A[i,k] B[j,k]| (softmax weights  */
+/* are already positive).  scores[h * nnz + e] = e_h of entry e and           */
+/* lse[q * H + h] = m + log(sum) (-inf for an empty row) when requested.      */
+/* ------------------------------------------------------------------------- */
+static void head_score(int dta, const void* A, int64_t lda, int dtb, const void* B, int64_t ldb, int64_t i,
+                       int64_t j, int64_t k0, int64_t D, double sv, double scale, double* score, double* score_abs)
+{
+    double dot = 0.0, dabs = 0.0;
+    for (int64_t k = k0; k < k0 + D; ++k) {
+        double t = elem(dta, A, i * lda + k, NULL, i) * elem(dtb, B, j * ldb + k, NULL, j);
+        dot += t;
+        dabs += fabs(t);
+    }
+    *score = scale * sv * dot;
+    *score_abs = fabs(scale * sv) * dabs;
+}
+
+int oracle_fusedmm(int64_t M, int64_t N, int64_t K, int64_t H,
+                   const int32_t* rowptr, const int32_t* colidx, const double* vals,
+                   double scale, int row_softmax, int abs_mode,
+                   int dta, const void* A, int64_t lda, int dtb, const void* B, int64_t ldb,
+                   int64_t nrows, const int64_t* rows, double* Y, double* scores, double* lse)
+{
+    if (H < 1 || K % H != 0) return 3;
+    int64_t D = K / H, nnz = rowptr[M];
+    int64_t count = rows ? nrows : M;
+    for (int64_t q = 0; q < count; ++q) {
+        int64_t i = rows ? rows[q] : q;
+        if (i < 0 || i >= M) return 1;
+        double* y = Y + q * K;
+        for (int64_t k = 0; k < K; ++k) y[k] = 0.0;
+        for (int64_t h = 0; h < H; ++h) {
+            int64_t k0 = h * D;
+            double m = -INFINITY, l = 0.0, sc, sa;
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                int64_t j = colidx[e];
+                if (j < 0 || j >= N) return 2;
+                head_score(dta, A, lda, dtb, B, ldb, i, j, k0, D, vals ? vals[e] : 1.0, scale, &sc, &sa);
+                if (scores) scores[h * nnz + e] = sc;
+                if (sc > m) m = sc;
+            }
+            if (row_softmax)
+                for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                    head_score(dta, A, lda, dtb, B, ldb, i, colidx[e], k0, D, vals ? vals[e] : 1.0, scale, &sc, &sa);
+                    l += exp(sc - m);
+                }
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                int64_t j = colidx[e];
+                head_score(dta, A, lda, dtb, B, ldb, i, j, k0, D, vals ? vals[e] : 1.0, scale, &sc, &sa);
+                double w = row_softmax ? exp(sc - m) / l : sc;
+                double wa = row_softmax ? w : sa;
+                for (int64_t k = k0; k < k0 + D; ++k) {
+                    double b = elem(dtb, B, j * ldb + k, NULL, j);
+                    y[k] += abs_mode ? wa * fabs(b) : w * b;
+                }
+            }
+            if (lse) lse[q * H + h] = (rowptr[i + 1] > rowptr[i]) ? m + log(l) : -INFINITY;
         }
     }
     return 0;

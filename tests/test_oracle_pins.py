@@ -361,3 +361,103 @@ def test_gnn_gradient_fd_scale12():
     for (i, k) in [(heavy, 0), (0, 3), (P.M - 1, 7)]:
         V = np.zeros_like(H); V[i, k] = 1.0
         assert abs(_fd(L, H, V) - dH[i, k]) <= 1e-6 * max(1.0, abs(dH[i, k]))
+
+
+# ----------------------------------------------------------------------------
+# FusedMM (SDDMM cascaded into SpMM, per head, optional row softmax)
+# ----------------------------------------------------------------------------
+
+def _dense_fused(rp, ci, vals, A, B, heads, scale, softmax):
+    """Dense FP64 reference: masked score matrix per head, masked row softmax."""
+    M, K = A.shape
+    N = B.shape[0]
+    D = K // heads
+    S = dense(rp, ci, vals, M, N)
+    mask = dense(rp, ci, None, M, N) > 0
+    Y = np.zeros((M, K))
+    lse = np.full((M, heads), -np.inf)
+    for h in range(heads):
+        sl = slice(h * D, (h + 1) * D)
+        E = scale * S * (A[:, sl].astype(np.float64) @ B[:, sl].astype(np.float64).T)
+        if softmax:
+            Em = np.where(mask, E, -np.inf)
+            m = Em.max(axis=1, keepdims=True)
+            P = np.where(mask, np.exp(Em - np.where(np.isfinite(m), m, 0.0)), 0.0)
+            l = P.sum(axis=1, keepdims=True)
+            W = np.divide(P, l, out=np.zeros_like(P), where=l > 0)
+            nz = mask.any(axis=1)
+            lse[nz, h] = (m + np.log(l))[nz, 0]
+        else:
+            W = np.where(mask, E, 0.0)
+        Y[:, sl] = W @ B[:, sl].astype(np.float64)
+    return Y, lse
+
+
+@pytest.mark.parametrize("heads,softmax", [(1, False), (2, False), (1, True), (4, True)])
+def test_fusedmm_dense_bruteforce(heads, softmax):
+    M, N, K = 37, 29, 16
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=heads * 10 + softmax)
+    Y, scores, lse = oracle.fusedmm(rp, ci, A, B, vals, heads=heads, scale=0.7, softmax=softmax)
+    Yd, lsed = _dense_fused(rp, ci, vals, A, B, heads, 0.7, softmax)
+    np.testing.assert_allclose(Y, Yd, rtol=1e-12, atol=1e-12)
+    if softmax:
+        np.testing.assert_allclose(lse, lsed, rtol=1e-12, atol=1e-12)
+    # scores are the SDDMM of each head's slice, scaled
+    D = K // heads
+    for h in range(heads):
+        sd = oracle.sddmm(rp, ci, A[:, h * D:(h + 1) * D], B[:, h * D:(h + 1) * D], vals)
+        np.testing.assert_allclose(scores[h], 0.7 * sd, rtol=1e-13, atol=1e-13)
+    rows = np.array([M - 1, 3, 0])
+    Ys, _, ls = oracle.fusedmm(rp, ci, A, B, vals, heads=heads, scale=0.7, softmax=softmax, rows=rows)
+    np.testing.assert_allclose(Ys, Y[rows], rtol=1e-14, atol=1e-14)
+
+
+def test_fusedmm_softmax_closed_forms():
+    g = np.random.default_rng(3)
+    N, K = 12, 8
+    B = g.standard_normal((N, K)).astype(np.float32)
+    # one nonzero per row: weight 1, Y = that B row, lse = its score
+    rp = np.arange(5, dtype=np.int32)
+    ci = np.array([3, 0, 11, 3], np.int32)
+    A = g.standard_normal((4, K)).astype(np.float32)
+    Y, sc, lse = oracle.fusedmm(rp, ci, A, B, softmax=True)
+    np.testing.assert_array_equal(Y, B[ci].astype(np.float64))
+    np.testing.assert_allclose(lse[:, 0], sc[0], rtol=0, atol=1e-15)
+    # all scores equal (A = 0): uniform weights, Y = mean of the row's B rows, lse = log(degree)
+    rp2 = np.array([0, 3, 3, 7], np.int32)
+    ci2 = np.array([1, 4, 9, 0, 2, 5, 11], np.int32)
+    Y2, _, lse2 = oracle.fusedmm(rp2, ci2, np.zeros((3, K), np.float32), B, softmax=True)
+    np.testing.assert_allclose(Y2[0], B[[1, 4, 9]].astype(np.float64).mean(0), rtol=1e-14, atol=1e-14)
+    np.testing.assert_array_equal(Y2[1], np.zeros(K))
+    np.testing.assert_allclose(Y2[2], B[[0, 2, 5, 11]].astype(np.float64).mean(0), rtol=1e-14, atol=1e-14)
+    assert lse2[1, 0] == -np.inf and abs(lse2[0, 0] - np.log(3)) < 1e-15 and abs(lse2[2, 0] - np.log(4)) < 1e-15
+    # one score above the others by 1000 (no overflow): weight 1 on it
+    Bo = np.eye(N, K, dtype=np.float32)
+    Ao = np.zeros((1, K), np.float32); Ao[0, 5] = 1000.0
+    rp3 = np.array([0, 4], np.int32); ci3 = np.array([2, 5, 6, 7], np.int32)
+    Y3, _, lse3 = oracle.fusedmm(rp3, ci3, Ao, Bo, softmax=True)
+    np.testing.assert_array_equal(Y3[0], Bo[5].astype(np.float64))
+    assert abs(lse3[0, 0] - 1000.0) < 1e-12
+    # a duplicated entry counts twice: two equal copies of one column share the weight
+    rp4 = np.array([0, 2], np.int32); ci4 = np.array([7, 7], np.int32)
+    Y4, _, lse4 = oracle.fusedmm(rp4, ci4, A[:1], B, softmax=True)
+    np.testing.assert_allclose(Y4[0], B[7].astype(np.float64), rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(lse4[0, 0], float(np.dot(A[0].astype(np.float64), B[7])) + np.log(2.0), rtol=1e-14)
+
+
+def test_fusedmm_plain_is_spmm_of_scores_and_absmode():
+    M, N, K = 30, 25, 12
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=5)
+    Y, sc, _ = oracle.fusedmm(rp, ci, A, B, vals, heads=3, scale=-1.5)
+    D = K // 3
+    Yabs, _, _ = oracle.fusedmm(rp, ci, A, B, vals, heads=3, scale=-1.5, absmode=True)
+    for h in range(3):
+        sl = slice(h * D, (h + 1) * D)
+        np.testing.assert_allclose(Y[:, sl], dense(rp, ci, sc[h], M, N) @ B[:, sl].astype(np.float64),
+                                   rtol=1e-12, atol=1e-12)
+        # denominator: |scale s| sum|a b| times |b|
+        ab = 1.5 * np.abs(vals.astype(np.float64)) * (np.abs(A[:, sl].astype(np.float64)) @ np.abs(B[:, sl].astype(np.float64)).T)[
+            np.repeat(np.arange(M), np.diff(rp)), ci]
+        np.testing.assert_allclose(Yabs[:, sl], dense(rp, ci, ab, M, N) @ np.abs(B[:, sl].astype(np.float64)),
+                                   rtol=1e-12, atol=1e-12)
+    assert np.all(Yabs >= np.abs(Y) - 1e-12)
