@@ -179,6 +179,28 @@ spk_status spk_spmm_static(spk_csr S, const float* vals, const float* vals2,
                            spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate,
                            const spk_tune* tune, void* stream);
 
+/* FusedMM: SDDMM cascaded into SpMM on one dense matrix (the cascade Sec. 2
+ * names; operands as in Eq. 1 and Eq. 2), per head of `heads` equal slices of
+ * K (head width dh = K / heads):
+ *   e_h(i,j) = scale * s_ij * <A[i, head h], B[j, head h]>
+ *   w_h(i,j) = e_h(i,j), or (softmax = 1) exp(e_h(i,j) - m) / sum over row i
+ *   Y[i, head h] = sum_j w_h(i,j) * B[j, head h]          (Y: M x K, FP32)
+ * Each gathered B row serves both products.  A (M x K) and B (N x K) share
+ * dtype dt (F32, BF16 or F16), 16-byte aligned with 16-byte row strides; dh
+ * must be a whole number of 16-byte vectors.  vals: NULL (ones) or 16-byte
+ * aligned FP32.  scores: NULL or heads x nnz FP32 (head-major, CSR order
+ * within a head) receiving e.  lse: NULL or M x heads FP32 receiving
+ * m + log(sum exp) of each row (softmax only; -inf for an empty row, whose Y
+ * row is 0).  Needs the balanced schedule; workspace >=
+ * spk_fusedmm_workspace_size bytes (16-byte aligned; NULL if that is 0).
+ * Split rows are merged in a fixed order: results are deterministic.  Calls
+ * that share one schedule must not overlap on the device. */
+spk_status spk_fusedmm_workspace_size(spk_csr S, int32_t K, int32_t heads, size_t* bytes);
+spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int32_t softmax, spk_dtype dt,
+                       const void* A, int64_t lda, const void* B, int64_t ldb, int32_t K, int32_t heads,
+                       float* Y, int64_t ldy, float* scores, float* lse,
+                       void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
+
 /* ----------------------------------------------------- transpose plan -- */
 /* The CSC of S by a stable device radix sort on the column index: colptr[N+1],
  * rowidx[nnz] (rows ascending inside a column) and perm[nnz] (CSR slot of each

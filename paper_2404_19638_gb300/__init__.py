@@ -4,6 +4,7 @@
     out = sddmm(S, A, B)                          # Eq. 1, FP32 per nonzero
     C = spmm(S, B)                                # Eq. 2
     X = spmm_t(S, Y)                              # S^T Y via the transpose plan
+    Y, _, _ = fusedmm(S, A, B, heads=4, softmax=True)   # SDDMM -> (softmax) -> SpMM in one kernel
 
 All arithmetic runs in libspk's CUDA kernels for sm_103a (include/spk.h);
 PyTorch supplies device memory and streams.  There is no CPU fallback: the
@@ -11,10 +12,10 @@ first call raises if libspk.so was not built.
 """
 from .binding import SpkError, Tune, library_path
 from .sparse import CSR, TransposePlan, DEFAULT_CHUNK_WORK
-from .ops import sddmm, spmm, spmm_t, cast, quantize_e4m3_rows
+from .ops import sddmm, spmm, spmm_t, fusedmm, cast, quantize_e4m3_rows
 from . import autograd
 from .batch import Batch, Item, OP_SDDMM, OP_SPMM
 from .autotune import Autotuner
 
-__all__ = ["CSR", "TransposePlan", "sddmm", "spmm", "spmm_t", "cast", "quantize_e4m3_rows", "autograd",
+__all__ = ["CSR", "TransposePlan", "sddmm", "spmm", "spmm_t", "fusedmm", "cast", "quantize_e4m3_rows", "autograd",
            "Batch", "Item", "OP_SDDMM", "OP_SPMM", "Autotuner", "SpkError", "Tune", "library_path", "DEFAULT_CHUNK_WORK"]

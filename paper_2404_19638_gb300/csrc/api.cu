@@ -402,6 +402,76 @@ extern "C" spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
 }
 
 // ----------------------------------------------------------------------------
+// FusedMM (SDDMM cascaded into SpMM), per head, optional row softmax
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_fusedmm_workspace_size(spk_csr S, int32_t K, int32_t heads, size_t* bytes)
+{
+    REQUIRE(S && bytes && K >= 1 && heads >= 1, SPK_ERR_ARG, "spk_fusedmm_workspace_size: bad argument");
+    *bytes = S->has_sched ? (size_t)S->npieces * (((size_t)K + 2 * (size_t)heads + 3) / 4 * 4) * 4 : 0;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int32_t softmax, spk_dtype dt,
+                                  const void* A, int64_t lda, const void* B, int64_t ldb, int32_t K, int32_t heads,
+                                  float* Y, int64_t ldy, float* scores, float* lse, void* workspace, size_t ws_bytes,
+                                  const spk_tune* tune, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_fusedmm: S is NULL");
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_fusedmm: pattern belongs to a transpose plan");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_fusedmm: needs spk_schedule_build first");
+    REQUIRE(dt == SPK_F32 || dt == SPK_BF16 || dt == SPK_F16, SPK_ERR_DTYPE, "spk_fusedmm: dtype must be F32, BF16 or F16");
+    REQUIRE(K >= 1 && heads >= 1 && K % heads == 0, SPK_ERR_SHAPE, "spk_fusedmm: K (%d) must be a multiple of heads (%d)",
+            K, heads);
+    REQUIRE(softmax == 0 || softmax == 1, SPK_ERR_ARG, "spk_fusedmm: softmax must be 0 or 1");
+    const int vecn = vec_elems(dt);
+    const int dh = K / heads;
+    REQUIRE(dh % vecn == 0, SPK_ERR_UNSUPPORTED, "spk_fusedmm: head width %d is not a multiple of %d elements", dh,
+            vecn);
+    REQUIRE(lda >= K && ldb >= K && ldy >= K, SPK_ERR_SHAPE, "spk_fusedmm: leading dimensions must be >= K");
+    REQUIRE(S->nnz == 0 || (A && B), SPK_ERR_ARG, "spk_fusedmm: NULL operand");
+    REQUIRE(S->M == 0 || Y, SPK_ERR_ARG, "spk_fusedmm: Y is NULL");
+    REQUIRE(aligned16(A) && aligned16(B) && aligned16(Y) && (lda * dt_bytes(dt)) % 16 == 0 &&
+                (ldb * dt_bytes(dt)) % 16 == 0 && ldy % 4 == 0,
+            SPK_ERR_SHAPE, "spk_fusedmm: A, B, Y must be 16-byte aligned with 16-byte row strides");
+    REQUIRE(!vals || aligned16(vals), SPK_ERR_ARG, "spk_fusedmm: vals must be 16-byte aligned");
+    const int nvh = dh / vecn;
+    int G, NV = 1, U = 4;
+    if (nvh <= 4) G = 4;
+    else if (nvh <= 8) G = 8;
+    else if (nvh <= 16) G = 16;
+    else if (nvh <= 32) { G = 32; U = 8; }
+    else { G = 32; NV = 2; }
+    if (tune && tune->group_lanes) G = tune->group_lanes;
+    if (tune && tune->vecs_per_lane) NV = tune->vecs_per_lane;
+    if (tune && tune->unroll) U = tune->unroll;
+    const int idx = fused_shape_index(G, NV, U);
+    REQUIRE(idx >= 0, SPK_ERR_UNSUPPORTED, "spk_fusedmm: no kernel for group_lanes=%d vecs_per_lane=%d unroll=%d", G,
+            NV, U);
+    REQUIRE(G * NV >= nvh, SPK_ERR_UNSUPPORTED, "spk_fusedmm: a group of %d x %d vectors cannot hold a head of %d",
+            G, NV, nvh);
+    const size_t need = (size_t)S->npieces * (((size_t)K + 2 * (size_t)heads + 3) / 4 * 4) * 4;
+    if (need > 0) {
+        REQUIRE(workspace && ws_bytes >= need, SPK_ERR_WORKSPACE, "spk_fusedmm: workspace has %zu bytes, needs %zu",
+                workspace ? ws_bytes : (size_t)0, need);
+        REQUIRE(aligned16(workspace), SPK_ERR_WORKSPACE, "spk_fusedmm: workspace must be 16-byte aligned");
+    }
+    if (S->M == 0) return SPK_OK;
+    FusedArgs a;
+    a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = K; a.heads = heads; a.dh = dh;
+    a.softmax = softmax; a.scale = scale;
+    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx; a.vals = vals;
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.Y = Y; a.ldy = ldy; a.scores = scores; a.lse = lse;
+    a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
+    a.carry = reinterpret_cast<float*>(workspace);
+    a.nchunks = S->nchunks;
+    Launch L;
+    L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;
+    cudaError_t e = launch_fused(dt, L, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_fusedmm");
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
 // SpMM with library-held scratch
 // ----------------------------------------------------------------------------
 // Carry slots of spk_spmm_static.  A file-scope device array: every GPU that

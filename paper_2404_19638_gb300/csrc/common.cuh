@@ -306,6 +306,33 @@ struct SpmmArgs {
     int64_t nchunks;
 };
 
+// FusedMM: SDDMM cascaded into SpMM on one dense matrix B, per head of
+// heads equal slices of K (dh = K / heads): scores e = scale * s * <a_i, b_j>
+// over the head's slice, weights w = e or the row softmax of e, and
+// Y[i, head] = sum_j w_ij * B[j, head].
+struct FusedArgs {
+    int64_t M, N, nnz;
+    int32_t K, heads, dh;
+    int32_t softmax;
+    float scale;
+    const int32_t* rowptr;
+    const int32_t* colidx;
+    const int32_t* rowidx;
+    const float* vals;        // NULL = ones; 16-byte aligned
+    const void* A; int64_t lda;
+    const void* B; int64_t ldb;
+    float* Y; int64_t ldy;
+    float* scores;            // heads x nnz (head-major), or NULL
+    float* lse;               // M x heads: max + log(sum) of each softmax row, or NULL
+    const int2* bnd;
+    const int4* meta;
+    const int32_t* head_s0;
+    const int32_t* slot_np;
+    int32_t* cnt;
+    float* carry;             // split-row pieces: K partial sums + (max, sum) per head, per slot
+    int64_t nchunks;
+};
+
 // Kernel shape: lanes per group, 16-byte vectors per lane, nonzeros in flight.
 struct Shape { int G, NV, U; };
 
@@ -374,6 +401,8 @@ struct TplanLayout {
     SchedLayout sl;
 };
 TplanLayout tplan_layout(int64_t M, int64_t N, int64_t nnz, int32_t W);
+cudaError_t launch_fused(int dt, const Launch& L, const FusedArgs& a, cudaStream_t s);
+int fused_shape_index(int G, int NV, int U);   // -1 if not compiled
 cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const float* vals2, int64_t nnz, float* out,
                                 cudaStream_t s);
 cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,

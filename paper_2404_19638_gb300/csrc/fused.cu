@@ -1,0 +1,482 @@
+// FusedMM: SDDMM cascaded into SpMM (Sec. 2 names the cascade; operands as in
+// Eq. 1 and Eq. 2), on one gathered dense matrix B:
+//   e_h(i,j) = scale * s_ij * <A[i, head h], B[j, head h]>
+//   w_h(i,j) = e_h(i,j), or the softmax of e_h(i, .) over row i
+//   Y[i, head h] = sum_j w_h(i,j) * B[j, head h]
+// Every gathered row of B serves both products: one gather per nonzero and
+// head instead of two, and the scores never travel through HBM (they are
+// written only if asked for).
+//
+// Structure: the SpMM ring span (ring.cuh) with one lane group per span of the
+// balanced schedule and one head per grid row (blockIdx.y); a group covers a
+// whole head, so each score is complete after a butterfly all-reduce across
+// the group.  The A slice of the current row arrives through the ring when a
+// batch starts a new row.  Row softmax is online: the group keeps the running
+// maximum m, the running sum l and the unnormalised row acc, rescaling by
+// exp(m_old - m_new) once per batch.  A row split across chunks leaves
+// (acc, m, l) of each piece in its carry slot; the last piece to arrive merges
+// them in slot order (log-sum-exp) and writes the row, so results do not
+// depend on scheduling.
+#include "ring.cuh"
+
+namespace spk {
+
+#define SPK_FUSED_SHAPES(X) \
+    X(0, 4, 1, 4)           \
+    X(1, 8, 1, 4)           \
+    X(2, 16, 1, 4)          \
+    X(3, 32, 1, 8)          \
+    X(4, 32, 2, 4)
+
+constexpr int kFusedShapes = 5;
+static const Shape kFusedShapeList[kFusedShapes] = {
+#define X(i, G_, NV_, U_) {G_, NV_, U_},
+    SPK_FUSED_SHAPES(X)
+#undef X
+};
+
+int fused_shape_index(int G, int NV, int U)
+{
+    for (int i = 0; i < kFusedShapes; ++i)
+        if (kFusedShapeList[i].G == G && kFusedShapeList[i].NV == NV && kFusedShapeList[i].U == U) return i;
+    return -1;
+}
+
+// Shared memory of one warp: B slots, the row/value tiles of the SpMM ring,
+// and one A slot per batch slot.
+__host__ __device__ constexpr int fused_ring_bytes(int NV, int U) { return spmm_ring_bytes(NV, U) + 2 * NV * 512; }
+
+template <int G>
+__device__ __forceinline__ float group_allreduce(const Group<G>& g, float x)
+{
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) x += __shfl_xor_sync(g.mask, x, d, G);
+    return x;
+}
+
+// Slot stride of the carry area, in floats: K partial sums and (max, sum)
+// per head, rounded up to 4 floats so that every slot is 16-byte aligned.
+__device__ __forceinline__ int64_t fused_slot_floats(const FusedArgs& a)
+{
+    return ((int64_t)a.K + 2 * a.heads + 3) / 4 * 4;
+}
+
+template <int VECN, int G, int NV>
+__device__ __forceinline__ void fused_write_row(const FusedArgs& a, const Group<G>& g, int kb, int nvh, int64_t row,
+                                                const float (&acc)[NV][VECN], float m, float l)
+{
+    const float inv = (a.softmax && l > 0.f) ? 1.f / l : 1.f;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = t * G + g.gl;
+        if (v >= nvh) continue;
+        float o[VECN];
+#pragma unroll
+        for (int q = 0; q < VECN; ++q) o[q] = (a.softmax && !(l > 0.f)) ? 0.f : acc[t][q] * inv;
+        store_elems<DT_F32, VECN>(a.Y, row * a.ldy + (int64_t)kb * a.dh + (int64_t)v * VECN, o);
+    }
+    if (a.softmax && a.lse && g.gl == 0) a.lse[row * a.heads + kb] = (l > 0.f) ? m + logf(l) : -INFINITY;
+}
+
+template <int VECN, int G, int NV>
+__device__ __forceinline__ void fused_zero_row(const FusedArgs& a, const Group<G>& g, int kb, int nvh, int64_t row)
+{
+    float z[NV][VECN];
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+#pragma unroll
+        for (int q = 0; q < VECN; ++q) z[t][q] = 0.f;
+    fused_write_row<VECN, G, NV>(a, g, kb, nvh, row, z, -INFINITY, 0.f);
+}
+
+// Deposit one piece of a split row; the last piece to arrive (over all
+// pieces and heads) merges them in slot order and writes the row.
+template <int VECN, int G, int NV>
+__device__ __forceinline__ void fused_finish_piece(const FusedArgs& a, const Group<G>& g, int kb, int nvh, int slot,
+                                                   int s0, int64_t row, const float (&acc)[NV][VECN], float m,
+                                                   float l)
+{
+    const int64_t sf = fused_slot_floats(a);
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int v = t * G + g.gl;
+        if (v < nvh) store_elems<DT_F32, VECN>(a.carry, (int64_t)slot * sf + (int64_t)kb * a.dh + (int64_t)v * VECN, acc[t]);
+    }
+    if (g.gl == 0) {
+        a.carry[(int64_t)slot * sf + a.K + 2 * kb] = m;
+        a.carry[(int64_t)slot * sf + a.K + 2 * kb + 1] = l;
+    }
+    __threadfence();
+    __syncwarp(g.mask);
+    int last = 0;
+    if (g.gl == 0) {
+        const int np = __ldcg(a.slot_np + s0);
+        const int old = atomicAdd(a.cnt + s0, 1);
+        last = (old == np * a.heads - 1);
+    }
+    last = __shfl_sync(g.mask, last, 0, G);
+    if (!last) return;
+    __threadfence();
+    const int np = __ldcg(a.slot_np + s0);
+    for (int h = 0; h < a.heads; ++h) {
+        float M = -INFINITY;
+        if (a.softmax)
+            for (int sl = s0; sl < s0 + np; ++sl) M = fmaxf(M, __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * h));
+        float L = 0.f;
+        float sum[NV][VECN];
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int q = 0; q < VECN; ++q) sum[t][q] = 0.f;
+        for (int sl = s0; sl < s0 + np; ++sl) {
+            float c = 1.f;
+            if (a.softmax) {
+                const float mp = __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * h);
+                const float lp = __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * h + 1);
+                c = (lp > 0.f) ? expf(mp - M) : 0.f;
+                L += lp * c;
+            }
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                const int v = t * G + g.gl;
+                if (v >= nvh) continue;
+                float x[VECN];
+                load_elems_cg<DT_F32, VECN>(a.carry, (int64_t)sl * sf + (int64_t)h * a.dh + (int64_t)v * VECN, x);
+#pragma unroll
+                for (int q = 0; q < VECN; ++q) sum[t][q] = a.softmax ? fmaf(x[q], c, sum[t][q]) : sum[t][q] + x[q];
+            }
+        }
+        fused_write_row<VECN, G, NV>(a, g, h, nvh, row, sum, M, L);
+    }
+    __syncwarp(g.mask);
+    if (g.gl == 0) atomicExch(a.cnt + s0, 0);   // ready for the next launch
+}
+
+template <int DT, int G, int NV, int U, bool ALLV>
+__device__ __forceinline__ void fused_span(const FusedArgs& a, const Group<G>& g, uint4* wring, int kb, int r0,
+                                           int e0, int r1, int e1, const int4 meta, int head_s0)
+{
+    constexpr int VECN = vec_elems(DT);
+    constexpr int TG = 4 * G;
+    static_assert(U % 4 == 0 && TG % U == 0 && TG / U >= 2 && U <= G, "batches must tile the group tile");
+    const int gl = g.gl;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G;
+    const int nvh = a.dh / VECN;
+    bool vin[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) vin[t] = ALLV || (t * G + gl < nvh);
+    const int64_t hoff = (int64_t)kb * a.dh * dt_bytes(DT);           // byte offset of the head's slice
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + hoff + gl * 16;
+    const char* __restrict__ Ab = reinterpret_cast<const char*>(a.A) + hoff + gl * 16;
+    const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DT);
+    const unsigned lda_bytes = (unsigned)a.lda * dt_bytes(DT);
+    const float* __restrict__ vals = a.vals;
+    int* trow = reinterpret_cast<int*>(wring + 2 * U * NV * 32) + grp * TG;
+    float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wring + 2 * U * NV * 32) + 2 * 128) + grp * TG;
+    uint4* ringA = reinterpret_cast<uint4*>(reinterpret_cast<int*>(wring + 2 * U * NV * 32) + 4 * 128);
+    const float scale = a.scale;
+    const bool smax = a.softmax != 0;
+
+    float acc[NV][VECN], av[NV][VECN];
+#pragma unroll
+    for (int t = 0; t < NV; ++t)
+#pragma unroll
+        for (int q = 0; q < VECN; ++q) { acc[t][q] = 0.f; av[t][q] = 0.f; }
+    float m = -INFINITY, l = 0.f;
+    int cur = r0;            // output row being accumulated
+    int acur = -1;           // row whose A slice is in av
+    auto flush = [&](int row) {
+        if (row == r0 && meta.x >= 0)
+            fused_finish_piece<VECN, G, NV>(a, g, kb, nvh, meta.x, head_s0, row, acc, m, l);
+        else if (row == r1 && meta.y >= 0)
+            fused_finish_piece<VECN, G, NV>(a, g, kb, nvh, meta.y, meta.y, row, acc, m, l);
+        else
+            fused_write_row<VECN, G, NV>(a, g, kb, nvh, row, acc, m, l);
+    };
+    auto reset = [&]() {
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
+        m = -INFINITY;
+        l = 0.f;
+    };
+    // one gathered row: partial dot of the lane's slice with the current A slice
+    auto partial = [&](const uint4* sl, int u) {
+        float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            if (!vin[t]) continue;
+            const uint4 v = sl[(u * NV + t) * 32];
+            Raw<DT, VECN> rb;
+            rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
+            float bf[VECN];
+            unpack_all<DT, VECN>(rb, bf);
+            dot_pairs<VECN>(d2, av[t], bf);
+        }
+        return d2.x + d2.y;
+    };
+    auto accumulate = [&](const uint4* sl, int u, float w) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            if (!vin[t]) continue;
+            const uint4 v = sl[(u * NV + t) * 32];
+            Raw<DT, VECN> rb;
+            rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
+            float bf[VECN];
+            unpack_all<DT, VECN>(rb, bf);
+            axpy_pairs<VECN>(acc[t], w, bf);
+        }
+    };
+    auto rescale = [&](float c) {
+#pragma unroll
+        for (int t = 0; t < NV; ++t)
+#pragma unroll
+            for (int q = 0; q < VECN; ++q) acc[t][q] *= c;
+    };
+
+    if (e0 < e1) {
+        const int tb0 = e0 & ~3;
+        const int nb = (e1 - tb0 + U - 1) / U;
+        // columns and COO rows of tile t in registers (they address the gathers
+        // and the A slices); rows and values also go to the shared tile for the compute
+        auto cols = [&](int t, int4& c, int4& r) {
+            const int e = tb0 + t * TG + 4 * gl;
+            if (e + 4 <= e1) {
+                c = ld4(a.colidx + e);
+                r = ld4(a.rowidx + e);
+                return;
+            }
+            c = make_int4(0, 0, 0, 0);
+            r = make_int4(0, 0, 0, 0);
+            if (e < e1) { c.x = __ldg(a.colidx + e); r.x = __ldg(a.rowidx + e); }
+            if (e + 1 < e1) { c.y = __ldg(a.colidx + e + 1); r.y = __ldg(a.rowidx + e + 1); }
+            if (e + 2 < e1) { c.z = __ldg(a.colidx + e + 2); r.z = __ldg(a.rowidx + e + 2); }
+        };
+        auto stage_tile = [&](int t) {
+            const int e = tb0 + t * TG + 4 * gl;
+            const int n = e1 - e;
+            if (n <= 0) return;
+            const int bytes = n >= 4 ? 16 : 4 * n;
+            const int o = (t & 1) * 128 + 4 * gl;
+            cp_async16(trow + o, a.rowidx + e, bytes);
+            if (vals) cp_async16(tval + o, vals + e, bytes);
+        };
+        int4 tc, tr, nc, nr;
+        cols(0, tc, tr);
+        cols(1, nc, nr);
+        int itile = 0;
+        int ilast = -1;
+        stage_tile(0);
+        auto issue = [&](int b) {
+            if (b < nb) {
+                const int t = (b * U) / TG;
+                if (t != itile) {
+                    tc = nc; tr = nr;
+                    cols(t + 1, nc, nr);
+                    stage_tile(t);
+                    itile = t;
+                }
+                const int src0 = ((b * U) % TG) >> 2;
+                int j[U], rws[U];
+#pragma unroll
+                for (int c = 0; c < U / 4; ++c) {
+                    j[4 * c + 0] = __shfl_sync(g.mask, tc.x, src0 + c, G);
+                    j[4 * c + 1] = __shfl_sync(g.mask, tc.y, src0 + c, G);
+                    j[4 * c + 2] = __shfl_sync(g.mask, tc.z, src0 + c, G);
+                    j[4 * c + 3] = __shfl_sync(g.mask, tc.w, src0 + c, G);
+                    rws[4 * c + 0] = __shfl_sync(g.mask, tr.x, src0 + c, G);
+                    rws[4 * c + 1] = __shfl_sync(g.mask, tr.y, src0 + c, G);
+                    rws[4 * c + 2] = __shfl_sync(g.mask, tr.z, src0 + c, G);
+                    rws[4 * c + 3] = __shfl_sync(g.mask, tr.w, src0 + c, G);
+                }
+                const int eb = tb0 + b * U;
+                uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
+                bool copied = false;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (eb + u < e0 || eb + u >= e1) continue;
+                    const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
+#pragma unroll
+                    for (int t2 = 0; t2 < NV; ++t2)
+                        if (vin[t2]) cpa16(sl + (u * NV + t2) * 32, brow + t2 * G * 16);
+                    if (rws[u] != ilast) {
+                        if (!copied) {
+                            copied = true;
+                            const char* arow = Ab + (size_t)(unsigned)rws[u] * lda_bytes;
+#pragma unroll
+                            for (int t2 = 0; t2 < NV; ++t2)
+                                if (vin[t2]) cpa16(ringA + ((b & 1) * NV + t2) * 32 + lane, arow + t2 * G * 16);
+                        }
+                        ilast = rws[u];
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+
+        issue(0);
+        for (int b = 0; b < nb; ++b) {
+            __syncwarp(g.mask);
+            issue(b + 1);
+            cp_async_wait<1>();
+            __syncwarp(g.mask);
+            const int eb = tb0 + b * U;
+            const uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
+            const int o = (((b * U) / TG) & 1) * 128 + (b * U) % TG;
+            int rc[U];
+            float sc[U];
+#pragma unroll
+            for (int c = 0; c < U / 4; ++c) {
+                const int4 r4 = *reinterpret_cast<const int4*>(trow + o + 4 * c);
+                rc[4 * c + 0] = r4.x; rc[4 * c + 1] = r4.y; rc[4 * c + 2] = r4.z; rc[4 * c + 3] = r4.w;
+                if (vals) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(tval + o + 4 * c);
+                    sc[4 * c + 0] = v4.x; sc[4 * c + 1] = v4.y; sc[4 * c + 2] = v4.z; sc[4 * c + 3] = v4.w;
+                } else {
+                    sc[4 * c + 0] = sc[4 * c + 1] = sc[4 * c + 2] = sc[4 * c + 3] = 1.f;
+                }
+            }
+            float ev[U];
+            if (eb >= e0 && eb + U <= e1 && rc[U - 1] == cur && cur == acur) {
+                // the whole batch continues the current row: U scores, one rescale
+#pragma unroll
+                for (int u = 0; u < U; ++u) ev[u] = scale * (sc[u] * group_allreduce<G>(g, partial(sl, u)));
+                if (smax) {
+                    float mb = m;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) mb = fmaxf(mb, ev[u]);
+                    const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
+                    rescale(c);
+                    l *= c;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float w = expf(ev[u] - mb);
+                        l += w;
+                        accumulate(sl, u, w);
+                    }
+                    m = mb;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) accumulate(sl, u, ev[u]);
+                }
+            } else {
+                bool first = true;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    ev[u] = 0.f;
+                    const int e = eb + u;
+                    if (e < e0 || e >= e1) continue;
+                    if (rc[u] != cur) {
+                        flush(cur);
+                        for (int rr = cur + 1; rr < rc[u]; ++rr) fused_zero_row<VECN, G, NV>(a, g, kb, nvh, rr);
+                        cur = rc[u];
+                        reset();
+                    }
+                    if (rc[u] != acur) {
+                        if (first) {
+#pragma unroll
+                            for (int t = 0; t < NV; ++t)
+                                if (vin[t]) {
+                                    const uint4 v = ringA[((b & 1) * NV + t) * 32 + lane];
+                                    Raw<DT, VECN> ra;
+                                    ra.w[0] = v.x; ra.w[1] = v.y; ra.w[2] = v.z; ra.w[3] = v.w;
+                                    unpack_all<DT, VECN>(ra, av[t]);
+                                }
+                        } else {
+                            const char* arow = reinterpret_cast<const char*>(a.A) + hoff + (size_t)(unsigned)rc[u] * lda_bytes;
+#pragma unroll
+                            for (int t = 0; t < NV; ++t)
+                                if (vin[t]) load_elems<DT, VECN>(arow, (int64_t)(t * G + gl) * VECN, av[t]);
+                        }
+                        first = false;
+                        acur = rc[u];
+                    }
+                    ev[u] = scale * (sc[u] * group_allreduce<G>(g, partial(sl, u)));
+                    if (smax) {
+                        const float mb = fmaxf(m, ev[u]);
+                        const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
+                        rescale(c);
+                        const float w = expf(ev[u] - mb);
+                        l = l * c + w;
+                        accumulate(sl, u, w);
+                        m = mb;
+                    } else {
+                        accumulate(sl, u, ev[u]);
+                    }
+                }
+            }
+            if (a.scores) {
+                float mine = ev[0];
+#pragma unroll
+                for (int u = 1; u < U; ++u)
+                    if (gl == u) mine = ev[u];
+                const int e = eb + gl;
+                if (gl < U && e >= e0 && e < e1) __stcs(a.scores + (int64_t)kb * a.nnz + e, mine);
+            }
+        }
+        cp_async_wait<0>();
+        __syncwarp(g.mask);
+    }
+    flush(cur);
+    for (int rr = cur + 1; rr <= meta.z; ++rr) fused_zero_row<VECN, G, NV>(a, g, kb, nvh, rr);
+}
+
+template <int DT, int G, int NV, int U>
+__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(fused_ring_bytes(NV, U)) < 8 ? ring_min_ctas(fused_ring_bytes(NV, U)) : 8)
+    k_fused(const FusedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    const Group<G> g;
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (fused_ring_bytes(NV, U) / 16);
+    const int kb = blockIdx.y;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const bool allv = a.dh / vec_elems(DT) >= G * NV;
+    for (int64_t c = gid; c < a.nchunks; c += ngroups) {
+        const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+        const int4 m = a.meta[c];
+        if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
+        const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
+        if (allv) fused_span<DT, G, NV, U, true>(a, g, wring, kb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+        else fused_span<DT, G, NV, U, false>(a, g, wring, kb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    }
+}
+
+template <int DT>
+static cudaError_t launch_fused_t(const Launch& L, const FusedArgs& a, cudaStream_t s)
+{
+    const void* fn = nullptr;
+    switch (L.shape) {
+#define X(i, G_, NV_, U_) case i: fn = (const void*)&k_fused<DT, G_, NV_, U_>; break;
+        SPK_FUSED_SHAPES(X)
+#undef X
+    }
+    if (!fn) return cudaErrorInvalidValue;
+    const Shape sh = kFusedShapeList[L.shape];
+    if (a.nchunks <= 0) return cudaSuccess;
+    const int64_t groups_per_cta = RING_THREADS / sh.G;
+    int64_t blocks = (a.nchunks + groups_per_cta - 1) / groups_per_cta;
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    if (a.heads > 65535) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(RING_THREADS / 32) * fused_ring_bytes(sh.NV, sh.U);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)a.heads), dim3(RING_THREADS), args, smem, s);
+}
+
+cudaError_t launch_fused(int dt, const Launch& L, const FusedArgs& a, cudaStream_t s)
+{
+    switch (dt) {
+    case DT_F32: return launch_fused_t<DT_F32>(L, a, s);
+    case DT_BF16: return launch_fused_t<DT_BF16>(L, a, s);
+    case DT_F16: return launch_fused_t<DT_F16>(L, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace spk

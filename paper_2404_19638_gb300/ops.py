@@ -128,6 +128,38 @@ def spmm_t(S: CSR, Y: torch.Tensor, vals=None, vals2=None, *, y_scale=None, out:
     return out
 
 
+def fusedmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, *, heads: int = 1, scale: float = 1.0,
+            softmax: bool = False, want_scores: bool = False, want_lse: bool = False,
+            out: torch.Tensor | None = None, tune=None, use_default_vals: bool = True):
+    """FusedMM: SDDMM cascaded into SpMM on B, per head of ``heads`` equal
+    slices of K, optionally with row-softmax weights:
+    Y[i, h] = sum_j w_h(i, j) B[j, h],  w = scale * s * <A_i, B_j>  (or its
+    row softmax).  Returns (Y, scores or None, lse or None); scores is
+    heads x nnz, lse is M x heads (softmax only)."""
+    if vals is None and use_default_vals:
+        vals = S.vals
+    dta, lda = _dense(A, "A", S.device)
+    dtb, ldb = _dense(B, "B", S.device)
+    if dta != dtb:
+        raise TypeError("A and B must have the same dtype")
+    if A.size(0) != S.M or B.size(0) != S.N or A.size(1) != B.size(1):
+        raise ValueError("A must be M x K and B N x K")
+    K = A.size(1)
+    if out is None:
+        out = torch.empty((S.M, K), dtype=torch.float32, device=S.device)
+    if out.dtype != torch.float32 or out.shape != (S.M, K):
+        raise ValueError("out must be M x K float32")
+    _, ldy = _dense(out, "out", S.device)
+    vals = _vals(vals, S, "vals")
+    scores = torch.empty((heads, S.nnz), dtype=torch.float32, device=S.device) if want_scores else None
+    lse = torch.empty((S.M, heads), dtype=torch.float32, device=S.device) if (want_lse and softmax) else None
+    ws = S.fused_workspace(K, heads)
+    check(lib().spk_fusedmm(S.handle, _ptr(vals), float(scale), int(bool(softmax)), dta, A.data_ptr(), lda,
+                            B.data_ptr(), ldb, K, int(heads), out.data_ptr(), ldy, _ptr(scores), _ptr(lse),
+                            _ptr(ws), 0 if ws is None else ws.numel(), _tune(tune), _stream(S.device)), "spk_fusedmm")
+    return out, scores, lse
+
+
 def cast(x: torch.Tensor, dtype) -> torch.Tensor:
     """Round-to-nearest-even cast of an FP32 tensor to bfloat16 / float16."""
     if x.dtype != torch.float32 or not x.is_cuda:

@@ -120,6 +120,20 @@ class CSR:
             self._ws[K] = ws
         return ws
 
+    def fused_workspace(self, K: int, heads: int) -> torch.Tensor | None:
+        """Carry workspace of a FusedMM with K columns in `heads` heads (cached)."""
+        nbytes = ctypes.c_size_t()
+        check(lib().spk_fusedmm_workspace_size(self._h, int(K), int(heads), ctypes.byref(nbytes)),
+              "spk_fusedmm_workspace_size")
+        if nbytes.value == 0:
+            return None
+        key = ("fused", K, heads)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nbytes.value:
+            ws = _buffer(nbytes.value, self.device)
+            self._ws[key] = ws
+        return ws
+
     def transpose_plan(self, chunk_work: int | None = None) -> "TransposePlan":
         """The transpose plan of S: the attached one when ``chunk_work`` is None
         (built with the default chunk size on first use), else one of that
