@@ -280,7 +280,7 @@ def event_ms(fn, stream, flush, reps=5):
     return statistics.median(ts)
 
 
-def aux_measurements(spk, S, P, A32, A, dt, elt, flush, stream, args):
+def aux_measurements(spk, S, P, A32, A, B, dt, elt, flush, stream, args):
     """The other steps of the path on the same pattern, outside the timed step:
     setup (schedule, transpose plan; wall clock, includes their host work),
     S^T Y through the plan, and the precision conversions."""
@@ -315,9 +315,28 @@ def aux_measurements(spk, S, P, A32, A, dt, elt, flush, stream, args):
     t = event_ms(lambda: spk.quantize_e4m3_rows(A32), stream, flush)
     out["quantize_e4m3_ms"] = t
     out["quantize_e4m3_algo_gbs"] = (5 * n + 4 * A32.size(0)) / (t / 1e3) / 1e9
-    out["note"] = ("measured after the timed step on the same pattern; builds by wall clock, "
-                   "kernels by CUDA events with the L2 flushed")
+    # the GNN-layer cascade: scores e = SDDMM(S, A, B) become the values of SpMM(S_e, B)
+    Bd = B
+    e_buf = torch.empty(P.nnz, dtype=torch.float32, device=dev)
+    Yl = torch.empty((P.M, P.K), dtype=torch.float32, device=dev)
+
+    def layer_separate():
+        spk.sddmm(S, A, Bd, out=e_buf)
+        spk.spmm(S, Bd, e_buf, out=Yl)
+    out["layer_separate_ms"] = event_ms(layer_separate, stream, flush)
+    fb = 4 * (P.M + 1) + 12 * P.nnz + P.M * P.K * elt + P.N * P.K * elt + P.M * P.K * 4
+    for name, kw in (("fusedmm_ms", {}), ("fusedmm_softmax_ms", {"softmax": True}),
+                     ("fusedmm_softmax_4heads_ms", {"softmax": True, "heads": 4})):
+        if P.K % (4 * (16 // elt)) and "heads" in kw:
+            continue
+        t = event_ms(lambda: spk.fusedmm(S, A, Bd, out=Yl, **kw), stream, flush)
+        out[name] = t
+        out[name.replace("_ms", "_algo_gbs")] = fb / (t / 1e3) / 1e9
+    out["note"] = ("measured after the timed step on the same pattern; builds by wall clock, kernels by CUDA "
+                   "events with the L2 flushed; layer_separate = SDDMM then SpMM on its scores, fusedmm = the "
+                   "same layer in one kernel")
     return out
+
 
 
 def main(args):
@@ -441,7 +460,7 @@ def main(args):
             dist.destroy_process_group()
         return 0
 
-    aux = None if args.no_aux else aux_measurements(spk, S, P, A32, A, dt, elt, flush, stream, args)
+    aux = None if args.no_aux else aux_measurements(spk, S, P, A32, A, B, dt, elt, flush, stream, args)
 
     pk, pk_kind = peaks()
     ab = algorithmic_bytes(P, elt)

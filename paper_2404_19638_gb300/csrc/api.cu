@@ -464,9 +464,19 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
     a.carry = reinterpret_cast<float*>(workspace);
     a.nchunks = S->nchunks;
-    Launch L;
-    L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;
-    cudaError_t e = launch_fused(dt, L, a, (cudaStream_t)stream);
+    // all heads in one lane group when a row is at most 32 vectors and the
+    // heads split the group evenly (unless a shape was asked for)
+    const int nv = K / vecn;
+    const bool shaped = tune && (tune->group_lanes || tune->vecs_per_lane || tune->unroll);
+    const bool mh = !shaped && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 && nv / heads >= 1;
+    cudaError_t e;
+    if (mh) {
+        e = launch_fused_mh(dt, nv, a, (cudaStream_t)stream);
+    } else {
+        Launch L;
+        L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;
+        e = launch_fused(dt, L, a, (cudaStream_t)stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "spk_fusedmm");
     return SPK_OK;
 }

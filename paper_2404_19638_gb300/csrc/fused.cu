@@ -112,7 +112,7 @@ __device__ __forceinline__ void fused_finish_piece(const FusedArgs& a, const Gro
     if (g.gl == 0) {
         const int np = __ldcg(a.slot_np + s0);
         const int old = atomicAdd(a.cnt + s0, 1);
-        last = (old == np * a.heads - 1);
+        last = (old == np * (int)gridDim.y - 1);     // every piece of every grid row (head) has arrived
     }
     last = __shfl_sync(g.mask, last, 0, G);
     if (!last) return;
@@ -442,6 +442,395 @@ __global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(fused_ring_bytes(N
         if (allv) fused_span<DT, G, NV, U, true>(a, g, wring, kb, b0.x, b0.y, b1.x, b1.y, m, hs0);
         else fused_span<DT, G, NV, U, false>(a, g, wring, kb, b0.x, b0.y, b1.x, b1.y, m, hs0);
     }
+}
+
+// ----------------------------------------------------------------------------
+// All heads in one group: G = K / VECN lanes, lane gl holds vector gl of every
+// row, the heads are consecutive blocks of NH = G / heads lanes.  A gathered
+// row serves every head; each head's scores come from a reduction over its
+// NH lanes, after which every lane of the head holds the same scores and the
+// same softmax state (m, l).  The split-row carry slot holds the K partial
+// sums and (m, l) per head; one arrival per piece.
+// ----------------------------------------------------------------------------
+template <int G, int U>
+__device__ __forceinline__ void head_allreduce(const Group<G>& g, int NH, float (&p)[U])
+{
+    if (NH >= U) {
+        // reduce-scatter over the low log2(U) lane bits, butterflies over the
+        // rest of the head, then every lane fetches the U sums of its head
+#pragma unroll
+        for (int dd = U / 2; dd >= 1; dd >>= 1) {
+            const bool upper = (g.gl & dd) != 0;
+#pragma unroll
+            for (int i = 0; i < dd; ++i) {
+                const float send = upper ? p[i] : p[i + dd];
+                const float keep = upper ? p[i + dd] : p[i];
+                p[i] = keep + __shfl_xor_sync(g.mask, send, dd, G);
+            }
+        }
+        for (int dd = U; dd < NH; dd <<= 1) p[0] += __shfl_xor_sync(g.mask, p[0], dd, G);
+        const int base = g.gl & ~(NH - 1);
+        const float mine = p[0];
+#pragma unroll
+        for (int u = 0; u < U; ++u) p[u] = __shfl_sync(g.mask, mine, base + u, G);
+    } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            for (int dd = NH / 2; dd >= 1; dd >>= 1) p[u] += __shfl_xor_sync(g.mask, p[u], dd, G);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ float head_allreduce1(const Group<G>& g, int NH, float x)
+{
+    for (int dd = NH / 2; dd >= 1; dd >>= 1) x += __shfl_xor_sync(g.mask, x, dd, G);
+    return x;
+}
+
+template <int VECN, int G>
+__device__ __forceinline__ void mh_write_row(const FusedArgs& a, const Group<G>& g, int hl, bool hlead, int64_t row,
+                                             const float (&acc)[VECN], float m, float l)
+{
+    const bool empty = a.softmax && !(l > 0.f);
+    const float inv = (a.softmax && l > 0.f) ? 1.f / l : 1.f;
+    float o[VECN];
+#pragma unroll
+    for (int q = 0; q < VECN; ++q) o[q] = empty ? 0.f : acc[q] * inv;
+    store_elems<DT_F32, VECN>(a.Y, row * a.ldy + (int64_t)g.gl * VECN, o);
+    if (a.softmax && a.lse && hlead) a.lse[row * a.heads + hl] = (l > 0.f) ? m + logf(l) : -INFINITY;
+}
+
+template <int VECN, int G>
+__device__ __forceinline__ void mh_finish_piece(const FusedArgs& a, const Group<G>& g, int hl, bool hlead, int slot,
+                                                int s0, int64_t row, const float (&acc)[VECN], float m, float l)
+{
+    const int64_t sf = fused_slot_floats(a);
+    store_elems<DT_F32, VECN>(a.carry, (int64_t)slot * sf + (int64_t)g.gl * VECN, acc);
+    if (hlead) {
+        a.carry[(int64_t)slot * sf + a.K + 2 * hl] = m;
+        a.carry[(int64_t)slot * sf + a.K + 2 * hl + 1] = l;
+    }
+    __threadfence();
+    __syncwarp(g.mask);
+    int last = 0;
+    if (g.gl == 0) {
+        const int np = __ldcg(a.slot_np + s0);
+        const int old = atomicAdd(a.cnt + s0, 1);
+        last = (old == np - 1);
+    }
+    last = __shfl_sync(g.mask, last, 0, G);
+    if (!last) return;
+    __threadfence();
+    const int np = __ldcg(a.slot_np + s0);
+    float M = -INFINITY;
+    if (a.softmax)
+        for (int sl = s0; sl < s0 + np; ++sl) M = fmaxf(M, __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * hl));
+    float L = 0.f, sum[VECN];
+#pragma unroll
+    for (int q = 0; q < VECN; ++q) sum[q] = 0.f;
+    for (int sl = s0; sl < s0 + np; ++sl) {
+        float c = 1.f;
+        if (a.softmax) {
+            const float mp = __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * hl);
+            const float lp = __ldcg(a.carry + (int64_t)sl * sf + a.K + 2 * hl + 1);
+            c = (lp > 0.f) ? expf(mp - M) : 0.f;
+            L += lp * c;
+        }
+        float x[VECN];
+        load_elems_cg<DT_F32, VECN>(a.carry, (int64_t)sl * sf + (int64_t)g.gl * VECN, x);
+#pragma unroll
+        for (int q = 0; q < VECN; ++q) sum[q] = a.softmax ? fmaf(x[q], c, sum[q]) : sum[q] + x[q];
+    }
+    mh_write_row<VECN, G>(a, g, hl, hlead, row, sum, M, L);
+    __syncwarp(g.mask);
+    if (g.gl == 0) atomicExch(a.cnt + s0, 0);
+}
+
+template <int DT, int G, int U>
+__device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>& g, uint4* wring, int r0, int e0,
+                                              int r1, int e1, const int4 meta, int head_s0)
+{
+    constexpr int VECN = vec_elems(DT);
+    constexpr int TG = 4 * G;
+    static_assert(U % 4 == 0 && TG % U == 0 && TG / U >= 2 && U <= G, "batches must tile the group tile");
+    const int gl = g.gl;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G;
+    const int NH = G / a.heads;                     // lanes per head
+    const int hl = gl / NH;                         // this lane's head
+    const bool hlead = (gl % NH) == 0;
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + gl * 16;
+    const char* __restrict__ Ab = reinterpret_cast<const char*>(a.A) + gl * 16;
+    const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DT);
+    const unsigned lda_bytes = (unsigned)a.lda * dt_bytes(DT);
+    const float* __restrict__ vals = a.vals;
+    int* trow = reinterpret_cast<int*>(wring + 2 * U * 32) + grp * TG;
+    float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wring + 2 * U * 32) + 2 * 128) + grp * TG;
+    uint4* ringA = reinterpret_cast<uint4*>(reinterpret_cast<int*>(wring + 2 * U * 32) + 4 * 128);
+    const float scale = a.scale;
+    const bool smax = a.softmax != 0;
+
+    float acc[VECN], av[VECN];
+#pragma unroll
+    for (int q = 0; q < VECN; ++q) { acc[q] = 0.f; av[q] = 0.f; }
+    float m = -INFINITY, l = 0.f;
+    int cur = r0, acur = -1;
+    auto flush = [&](int row) {
+        if (row == r0 && meta.x >= 0) mh_finish_piece<VECN, G>(a, g, hl, hlead, meta.x, head_s0, row, acc, m, l);
+        else if (row == r1 && meta.y >= 0) mh_finish_piece<VECN, G>(a, g, hl, hlead, meta.y, meta.y, row, acc, m, l);
+        else mh_write_row<VECN, G>(a, g, hl, hlead, row, acc, m, l);
+    };
+    auto zero_out = [&](int row) {
+        float z[VECN];
+#pragma unroll
+        for (int q = 0; q < VECN; ++q) z[q] = 0.f;
+        mh_write_row<VECN, G>(a, g, hl, hlead, row, z, -INFINITY, 0.f);
+    };
+    auto unpack_v = [&](const uint4 v, float (&f)[VECN]) {
+        Raw<DT, VECN> r;
+        r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
+        unpack_all<DT, VECN>(r, f);
+    };
+    auto dot = [&](const float (&bf)[VECN]) {
+        float2 d2 = make_float2(0.f, 0.f);
+        dot_pairs<VECN>(d2, av, bf);
+        return d2.x + d2.y;
+    };
+
+    if (e0 < e1) {
+        const int tb0 = e0 & ~3;
+        const int nb = (e1 - tb0 + U - 1) / U;
+        auto cols = [&](int t, int4& c, int4& r) {
+            const int e = tb0 + t * TG + 4 * gl;
+            if (e + 4 <= e1) {
+                c = ld4(a.colidx + e);
+                r = ld4(a.rowidx + e);
+                return;
+            }
+            c = make_int4(0, 0, 0, 0);
+            r = make_int4(0, 0, 0, 0);
+            if (e < e1) { c.x = __ldg(a.colidx + e); r.x = __ldg(a.rowidx + e); }
+            if (e + 1 < e1) { c.y = __ldg(a.colidx + e + 1); r.y = __ldg(a.rowidx + e + 1); }
+            if (e + 2 < e1) { c.z = __ldg(a.colidx + e + 2); r.z = __ldg(a.rowidx + e + 2); }
+        };
+        auto stage_tile = [&](int t) {
+            const int e = tb0 + t * TG + 4 * gl;
+            const int n = e1 - e;
+            if (n <= 0) return;
+            const int bytes = n >= 4 ? 16 : 4 * n;
+            const int o = (t & 1) * 128 + 4 * gl;
+            cp_async16(trow + o, a.rowidx + e, bytes);
+            if (vals) cp_async16(tval + o, vals + e, bytes);
+        };
+        int4 tc, tr, nc, nr;
+        cols(0, tc, tr);
+        cols(1, nc, nr);
+        int itile = 0, ilast = -1;
+        stage_tile(0);
+        auto issue = [&](int b) {
+            if (b < nb) {
+                const int t = (b * U) / TG;
+                if (t != itile) {
+                    tc = nc; tr = nr;
+                    cols(t + 1, nc, nr);
+                    stage_tile(t);
+                    itile = t;
+                }
+                const int src0 = ((b * U) % TG) >> 2;
+                int j[U], rws[U];
+#pragma unroll
+                for (int c = 0; c < U / 4; ++c) {
+                    j[4 * c + 0] = __shfl_sync(g.mask, tc.x, src0 + c, G);
+                    j[4 * c + 1] = __shfl_sync(g.mask, tc.y, src0 + c, G);
+                    j[4 * c + 2] = __shfl_sync(g.mask, tc.z, src0 + c, G);
+                    j[4 * c + 3] = __shfl_sync(g.mask, tc.w, src0 + c, G);
+                    rws[4 * c + 0] = __shfl_sync(g.mask, tr.x, src0 + c, G);
+                    rws[4 * c + 1] = __shfl_sync(g.mask, tr.y, src0 + c, G);
+                    rws[4 * c + 2] = __shfl_sync(g.mask, tr.z, src0 + c, G);
+                    rws[4 * c + 3] = __shfl_sync(g.mask, tr.w, src0 + c, G);
+                }
+                const int eb = tb0 + b * U;
+                uint4* sl = wring + (b & 1) * U * 32 + lane;
+                bool copied = false;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (eb + u < e0 || eb + u >= e1) continue;
+                    cpa16(sl + u * 32, Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+                    if (rws[u] != ilast) {
+                        if (!copied) {
+                            copied = true;
+                            cpa16(ringA + (b & 1) * 32 + lane, Ab + (size_t)(unsigned)rws[u] * lda_bytes);
+                        }
+                        ilast = rws[u];
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+
+        issue(0);
+        for (int b = 0; b < nb; ++b) {
+            __syncwarp(g.mask);
+            issue(b + 1);
+            cp_async_wait<1>();
+            __syncwarp(g.mask);
+            const int eb = tb0 + b * U;
+            const uint4* sl = wring + (b & 1) * U * 32 + lane;
+            const int o = (((b * U) / TG) & 1) * 128 + (b * U) % TG;
+            int rc[U];
+            float sc[U];
+#pragma unroll
+            for (int c = 0; c < U / 4; ++c) {
+                const int4 r4 = *reinterpret_cast<const int4*>(trow + o + 4 * c);
+                rc[4 * c + 0] = r4.x; rc[4 * c + 1] = r4.y; rc[4 * c + 2] = r4.z; rc[4 * c + 3] = r4.w;
+                if (vals) {
+                    const float4 v4 = *reinterpret_cast<const float4*>(tval + o + 4 * c);
+                    sc[4 * c + 0] = v4.x; sc[4 * c + 1] = v4.y; sc[4 * c + 2] = v4.z; sc[4 * c + 3] = v4.w;
+                } else {
+                    sc[4 * c + 0] = sc[4 * c + 1] = sc[4 * c + 2] = sc[4 * c + 3] = 1.f;
+                }
+            }
+            float ev[U];
+            if (eb >= e0 && eb + U <= e1 && rc[U - 1] == cur && cur == acur) {
+                float bf[U][VECN];
+#pragma unroll
+                for (int u = 0; u < U; ++u) unpack_v(sl[u * 32], bf[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) ev[u] = dot(bf[u]);
+                head_allreduce<G, U>(g, NH, ev);
+#pragma unroll
+                for (int u = 0; u < U; ++u) ev[u] = scale * (sc[u] * ev[u]);
+                if (smax) {
+                    float mb = m;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) mb = fmaxf(mb, ev[u]);
+                    const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
+#pragma unroll
+                    for (int q = 0; q < VECN; ++q) acc[q] *= c;
+                    l *= c;
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float w = expf(ev[u] - mb);
+                        l += w;
+                        axpy_pairs<VECN>(acc, w, bf[u]);
+                    }
+                    m = mb;
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) axpy_pairs<VECN>(acc, ev[u], bf[u]);
+                }
+            } else {
+                // span edge or row change: all U dots first (the A slice switches
+                // where a new row starts), one reduction for the batch, then the
+                // rows are closed and accumulated in order
+                float bf[U][VECN];
+                bool first = true;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    ev[u] = 0.f;
+                    const int e = eb + u;
+                    if (e < e0 || e >= e1) continue;
+                    unpack_v(sl[u * 32], bf[u]);
+                    if (rc[u] != acur) {
+                        if (first) unpack_v(ringA[(b & 1) * 32 + lane], av);
+                        else load_elems<DT, VECN>(reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)rc[u] * lda_bytes,
+                                                  (int64_t)gl * VECN, av);
+                        first = false;
+                        acur = rc[u];
+                    }
+                    ev[u] = dot(bf[u]);
+                }
+                head_allreduce<G, U>(g, NH, ev);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = eb + u;
+                    if (e < e0 || e >= e1) { ev[u] = 0.f; continue; }
+                    ev[u] = scale * (sc[u] * ev[u]);
+                    if (rc[u] != cur) {
+                        flush(cur);
+                        for (int rr = cur + 1; rr < rc[u]; ++rr) zero_out(rr);
+                        cur = rc[u];
+#pragma unroll
+                        for (int q = 0; q < VECN; ++q) acc[q] = 0.f;
+                        m = -INFINITY;
+                        l = 0.f;
+                    }
+                    if (smax) {
+                        const float mb = fmaxf(m, ev[u]);
+                        const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
+#pragma unroll
+                        for (int q = 0; q < VECN; ++q) acc[q] *= c;
+                        const float w = expf(ev[u] - mb);
+                        l = l * c + w;
+                        axpy_pairs<VECN>(acc, w, bf[u]);
+                        m = mb;
+                    } else {
+                        axpy_pairs<VECN>(acc, ev[u], bf[u]);
+                    }
+                }
+            }
+            if (a.scores && hlead) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int e = eb + u;
+                    if (e >= e0 && e < e1) __stcs(a.scores + (int64_t)hl * a.nnz + e, ev[u]);
+                }
+            }
+        }
+        cp_async_wait<0>();
+        __syncwarp(g.mask);
+    }
+    flush(cur);
+    for (int rr = cur + 1; rr <= meta.z; ++rr) zero_out(rr);
+}
+
+__host__ __device__ constexpr int fused_mh_ring_bytes(int U) { return fused_ring_bytes(1, U); }
+
+template <int DT, int G, int U>
+__global__ void __launch_bounds__(RING_THREADS, DT == DT_F32 ? 8 : 6) k_fused_mh(const FusedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char ring_smem[];
+    const Group<G> g;
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (fused_mh_ring_bytes(U) / 16);
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    for (int64_t c = gid; c < a.nchunks; c += ngroups) {
+        const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
+        const int4 m = a.meta[c];
+        if (b1.y == b0.y && m.z < b0.x) continue;
+        const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
+        fused_span_mh<DT, G, U>(a, g, wring, b0.x, b0.y, b1.x, b1.y, m, hs0);
+    }
+}
+
+template <int DT>
+static cudaError_t launch_fused_mh_t(int G, const FusedArgs& a, cudaStream_t s)
+{
+    const void* fn = nullptr;
+    switch (G) {
+    case 4: fn = (const void*)&k_fused_mh<DT, 4, 4>; break;
+    case 8: fn = (const void*)&k_fused_mh<DT, 8, 4>; break;
+    case 16: fn = (const void*)&k_fused_mh<DT, 16, 4>; break;
+    case 32: fn = (const void*)&k_fused_mh<DT, 32, 4>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (a.nchunks <= 0) return cudaSuccess;
+    const int64_t groups_per_cta = RING_THREADS / G;
+    int64_t blocks = (a.nchunks + groups_per_cta - 1) / groups_per_cta;
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
+    const size_t smem = (size_t)(RING_THREADS / 32) * fused_mh_ring_bytes(4);
+    void* args[] = {(void*)&a};
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks, 1), dim3(RING_THREADS), args, smem, s);
+}
+
+cudaError_t launch_fused_mh(int dt, int G, const FusedArgs& a, cudaStream_t s)
+{
+    switch (dt) {
+    case DT_F32: return launch_fused_mh_t<DT_F32>(G, a, s);
+    case DT_BF16: return launch_fused_mh_t<DT_BF16>(G, a, s);
+    case DT_F16: return launch_fused_mh_t<DT_F16>(G, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int DT>

@@ -29,7 +29,7 @@ def _case(M, N, K, seed, long_row=2500):
     return rp, ci, vals, A, B
 
 
-def _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W, seed_note=""):
+def _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W, seed_note="", tune=None):
     M, K = A.shape
     N = B.shape[0]
     scale = 1.0 / np.sqrt(K // heads)
@@ -43,7 +43,8 @@ def _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W, seed_note=""):
         fmt = "bf16" if dt == torch.bfloat16 else "f16"
         Aq = tA.view(torch.int16).cpu().numpy().view(np.uint16)
         Bq = tB.view(torch.int16).cpu().numpy().view(np.uint16)
-    Y, sc, lse = spk.fusedmm(S, tA, tB, heads=heads, scale=scale, softmax=softmax, want_scores=True, want_lse=True)
+    Y, sc, lse = spk.fusedmm(S, tA, tB, heads=heads, scale=scale, softmax=softmax, want_scores=True, want_lse=True,
+                             tune=tune)
     Yr, scr, lser = oracle.fusedmm(rp, ci, Aq, Bq, vals, heads=heads, scale=scale, softmax=softmax,
                                    fmt_a=fmt, fmt_b=fmt)
     Ya, _, _ = oracle.fusedmm(rp, ci, Aq, Bq, vals, heads=heads, scale=scale, softmax=softmax, fmt_a=fmt, fmt_b=fmt,
@@ -61,7 +62,7 @@ def _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W, seed_note=""):
         assert np.array_equal(np.isfinite(got), fin)
         assert np.max(np.abs(got[fin] - lser[fin]) / (1.0 + np.abs(lser[fin])), initial=0.0) <= 1e-5
     # deterministic (split rows are merged in a fixed order)
-    Y2, sc2, _ = spk.fusedmm(S, tA, tB, heads=heads, scale=scale, softmax=softmax, want_scores=True)
+    Y2, sc2, _ = spk.fusedmm(S, tA, tB, heads=heads, scale=scale, softmax=softmax, want_scores=True, tune=tune)
     assert torch.equal(Y, Y2) and torch.equal(sc, sc2)
     return S
 
@@ -71,6 +72,18 @@ def _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W, seed_note=""):
 def test_fused_f32(spk, K, heads, softmax):
     rp, ci, vals, A, B = _case(600, 450, K, seed=K + heads)
     _check(spk, rp, ci, vals, A, B, heads, softmax, torch.float32, W=128, seed_note=f"K={K} H={heads}")
+
+
+@pytest.mark.parametrize("shape", [(4, 1, 4), (8, 1, 4), (16, 1, 4), (32, 1, 8), (32, 2, 4)])
+def test_fused_head_per_grid_row(spk, shape):
+    """The kernel with one head per grid row (used for rows of more than 32
+    vectors, or when a shape is asked for)."""
+    G, NV, U = shape
+    K = 4 * G * NV
+    for heads in (1, 2):
+        rp, ci, vals, A, B = _case(400, 350, K * heads, seed=G + NV + heads)
+        _check(spk, rp, ci, vals, A, B, heads, heads == 2, torch.float32, W=64,
+               tune={"group_lanes": G, "vecs_per_lane": NV, "unroll": U})
 
 
 @pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
