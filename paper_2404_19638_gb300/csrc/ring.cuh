@@ -89,6 +89,58 @@ __device__ __forceinline__ void ring_fetch(const int4& t, int src0, int (&v)[U])
 }
 
 // ----------------------------------------------------------------------------
+// A slice of one lane (one 16-byte vector of the row of A).  FP32 keeps the
+// widened floats; BF16 / F16 keep the packed halves and multiply them with the
+// packed halves of B by mixed-precision FMAs (16-bit inputs, FP32 accumulate:
+// the product is exact and rounded once into the accumulator, the same result
+// as an fmaf on the widened values), so neither operand is unpacked.  Both
+// forms accumulate even elements in acc.x and odd ones in acc.y.
+// ----------------------------------------------------------------------------
+template <int DT>
+struct ASlice {
+    float f[4];
+    __device__ __forceinline__ void set(const uint4 v)
+    {
+        f[0] = __uint_as_float(v.x); f[1] = __uint_as_float(v.y); f[2] = __uint_as_float(v.z); f[3] = __uint_as_float(v.w);
+    }
+    __device__ __forceinline__ void zero() { f[0] = f[1] = f[2] = f[3] = 0.f; }
+    __device__ __forceinline__ void dot(float2& acc, const uint4 b) const
+    {
+        acc = __ffma2_rn(make_float2(f[0], f[1]), make_float2(__uint_as_float(b.x), __uint_as_float(b.y)), acc);
+        acc = __ffma2_rn(make_float2(f[2], f[3]), make_float2(__uint_as_float(b.z), __uint_as_float(b.w)), acc);
+    }
+};
+
+template <int DT>
+__device__ __forceinline__ void fma_halves(float2& acc, uint32_t a, uint32_t b)
+{
+    if constexpr (DT == DT_BF16)
+        asm("{\n .reg .b16 al, ah, bl, bh;\n mov.b32 {al, ah}, %2;\n mov.b32 {bl, bh}, %3;\n"
+            " fma.rn.f32.bf16 %0, al, bl, %0;\n fma.rn.f32.bf16 %1, ah, bh, %1;\n}"
+            : "+f"(acc.x), "+f"(acc.y) : "r"(a), "r"(b));
+    else
+        asm("{\n .reg .b16 al, ah, bl, bh;\n mov.b32 {al, ah}, %2;\n mov.b32 {bl, bh}, %3;\n"
+            " fma.rn.f32.f16 %0, al, bl, %0;\n fma.rn.f32.f16 %1, ah, bh, %1;\n}"
+            : "+f"(acc.x), "+f"(acc.y) : "r"(a), "r"(b));
+}
+
+template <int DT>
+struct ASlice16 {
+    uint4 w;
+    __device__ __forceinline__ void set(const uint4 v) { w = v; }
+    __device__ __forceinline__ void zero() { w = make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ void dot(float2& acc, const uint4 b) const
+    {
+        fma_halves<DT>(acc, w.x, b.x);
+        fma_halves<DT>(acc, w.y, b.y);
+        fma_halves<DT>(acc, w.z, b.z);
+        fma_halves<DT>(acc, w.w, b.w);
+    }
+};
+template <> struct ASlice<DT_BF16> : ASlice16<DT_BF16> {};
+template <> struct ASlice<DT_F16> : ASlice16<DT_F16> {};
+
+// ----------------------------------------------------------------------------
 // SDDMM (Eq. 1) over the span [e0, e1) of one warp; DT is the dtype of both
 // dense operands (F32, BF16 or F16).  ALLV: every lane's NV vectors lie
 // inside K (no per-vector predicates).
@@ -219,11 +271,9 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < D - 1; ++b) issue(b);
-    float av[NV][VECN];
+    ASlice<DT> av[NV];
 #pragma unroll
-    for (int t = 0; t < NV; ++t)
-#pragma unroll
-        for (int q = 0; q < VECN; ++q) av[t][q] = 0.f;
+    for (int t = 0; t < NV; ++t) av[t].zero();
     for (int b = 0; b < nb; ++b) {
         __syncwarp();
         issue(b + D - 1);
@@ -238,26 +288,14 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
             if (meta & 2) {                              // new row from nonzero 0 on: its A slice is in the ring
 #pragma unroll
                 for (int t = 0; t < NV; ++t)
-                    if (vin[t]) {
-                        const uint4 v = ringA[(d * NV + t) * 32 + lane];
-                        Raw<DT, VECN> ra;
-                        ra.w[0] = v.x; ra.w[1] = v.y; ra.w[2] = v.z; ra.w[3] = v.w;
-                        unpack_all<DT, VECN>(ra, av[t]);
-                    }
+                    if (vin[t]) av[t].set(ringA[(d * NV + t) * 32 + lane]);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    if (!vin[t]) continue;
-                    const uint4 v = sB[(u * NV + t) * 32];
-                    Raw<DT, VECN> rb;
-                    rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
-                    float bf[VECN];
-                    unpack_all<DT, VECN>(rb, bf);
-                    dot_pairs<VECN>(acc, av[t], bf);
-                }
+                for (int t = 0; t < NV; ++t)
+                    if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
                 p[u] = acc.x + acc.y;
             }
         } else {
@@ -272,31 +310,20 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
                     if (u == ua) {
 #pragma unroll
                         for (int t = 0; t < NV; ++t)
-                            if (vin[t]) {
-                                const uint4 v = ringA[(d * NV + t) * 32 + lane];
-                                Raw<DT, VECN> ra;
-                                ra.w[0] = v.x; ra.w[1] = v.y; ra.w[2] = v.z; ra.w[3] = v.w;
-                                unpack_all<DT, VECN>(ra, av[t]);
-                            }
+                            if (vin[t]) av[t].set(ringA[(d * NV + t) * 32 + lane]);
                     } else {
                         const int r = mrow[d * WB + grp * U + u];
-                        const char* arow = reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)r * lda_bytes;
+                        const uint4* arow = reinterpret_cast<const uint4*>(
+                            reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)r * lda_bytes) + gl;
 #pragma unroll
                         for (int t = 0; t < NV; ++t)
-                            if (vin[t]) load_elems<DT, VECN>(arow, (int64_t)(t * G + gl) * VECN, av[t]);
+                            if (vin[t]) av[t].set(__ldg(arow + t * G));
                     }
                 }
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    if (!vin[t]) continue;
-                    const uint4 v = sB[(u * NV + t) * 32];
-                    Raw<DT, VECN> rb;
-                    rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
-                    float bf[VECN];
-                    unpack_all<DT, VECN>(rb, bf);
-                    dot_pairs<VECN>(acc, av[t], bf);
-                }
+                for (int t = 0; t < NV; ++t)
+                    if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
                 p[u] = acc.x + acc.y;
             }
         }
