@@ -236,9 +236,15 @@ enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 // favours 4-lane groups with two vectors at 8 vectors a row and 8-lane groups
 // at 16; SpMM favours one vector a lane (16 lanes, 8 nonzeros in flight at
 // 16 vectors).
-static void default_shape(int op, int nvec, int* G, int* NV, int* U)
+static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16 = false)
 {
     *U = 4;
+    if (op != OP_SDDMM && half16) {
+        // 16-bit SpMM: 8-byte lane vectors over twice the lanes
+        if (nvec <= 4) { *G = 8; *NV = 1; return; }
+        if (nvec <= 8) { *G = 16; *NV = 1; *U = 8; return; }
+        if (nvec <= 16) { *G = 32; *NV = 1; *U = 8; return; }
+    }
     if (nvec <= 4) { *G = 4; *NV = 1; }
     else if (nvec <= 8) { *G = (op == OP_SDDMM) ? 4 : 8; *NV = (op == OP_SDDMM) ? 2 : 1; }
     else if (nvec <= 16) {
@@ -259,7 +265,8 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     const int vecn = vec ? vec_elems(dtb) : 1;
     const int nvec = K / vecn;
     int G, NV, U;
-    default_shape(op, nvec, &G, &NV, &U);
+    const bool half16 = vec && (variant == 2) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
+    default_shape(op, nvec, &G, &NV, &U, half16);
     if (t && t->group_lanes) G = t->group_lanes;
     if (t && t->vecs_per_lane) NV = t->vecs_per_lane;
     if (t && t->unroll) U = t->unroll;

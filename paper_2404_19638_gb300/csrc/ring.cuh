@@ -364,13 +364,48 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
 // 16-byte aligned without a second factor or a slot permutation (other calls
 // take the register path).
 // ----------------------------------------------------------------------------
-__host__ __device__ constexpr int spmm_ring_bytes(int NV, int U) { return 2 * U * NV * 512 + 2 * 2 * 128 * 4; }
+// VB: bytes of one lane vector, 16, or 8 for 16-bit operands spread over
+// twice the lanes (a group of G lanes then covers G * NV * VB bytes of a row).
+__host__ __device__ constexpr int spmm_ring_bytes(int NV, int U, int VB = 16)
+{
+    return 2 * U * NV * 32 * VB + 2 * 2 * 128 * 4;
+}
 
-template <int DT, int G, int NV, int U, bool ALLV>
-__device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>& g, uint4* wring, int kb, int nkb,
+__device__ __forceinline__ void cpa8(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+
+template <int VB>
+struct LaneVec { using type = uint4; };
+template <>
+struct LaneVec<8> { using type = uint2; };
+
+template <int DT, int VECN>
+__device__ __forceinline__ void unpack_vec(const uint4 v, float (&f)[VECN])
+{
+    Raw<DT, VECN> r;
+    r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
+    unpack_all<DT, VECN>(r, f);
+}
+template <int DT, int VECN>
+__device__ __forceinline__ void unpack_vec(const uint2 v, float (&f)[VECN])
+{
+    Raw<DT, VECN> r;
+    r.w[0] = v.x; r.w[1] = v.y;
+    unpack_all<DT, VECN>(r, f);
+}
+
+template <int DT, int G, int NV, int U, bool ALLV, int VB = 16>
+__device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>& g, uint4* wring16, int kb, int nkb,
                                                int r0, int e0, int r1, int e1, const int4 meta, int head_s0)
 {
-    constexpr int VECN = vec_elems(DT);
+    static_assert(VB == 16 || (VB == 8 && DT != DT_F32 && DT != DT_E4M3), "8-byte lane vectors are for 16-bit operands");
+    using Vec = typename LaneVec<VB>::type;
+    constexpr int VECN = VB / dt_bytes(DT);
+    Vec* wring = reinterpret_cast<Vec*>(wring16);
     constexpr int TG = 4 * G;                       // entries per group tile (one int4 per lane)
     static_assert(U % 4 == 0 && TG % U == 0 && TG / U >= 2, "batches must tile the group tile");
     const int gl = g.gl;
@@ -381,7 +416,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
     bool vin[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) vin[t] = ALLV || (vbase + t * G + gl < nvec);
-    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (vbase + gl) * 16;
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (vbase + gl) * VB;
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DT);
     const float* __restrict__ vals = a.vals;
     // tile buffers after the B slots: rows[2][128] then vals[2][128] per warp;
@@ -448,14 +483,17 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                 }
                 const int eb = tb0 + b * U;
                 const bool full = (eb >= e0) && (eb + U <= e1);
-                uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
+                Vec* sl = wring + (b & 1) * U * NV * 32 + lane;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (!full && (eb + u < e0 || eb + u >= e1)) continue;
                     const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
 #pragma unroll
                     for (int t2 = 0; t2 < NV; ++t2)
-                        if (vin[t2]) cpa16(sl + (u * NV + t2) * 32, brow + t2 * G * 16);
+                        if (vin[t2]) {
+                            if constexpr (VB == 16) cpa16(sl + (u * NV + t2) * 32, brow + t2 * G * 16);
+                            else cpa8(sl + (u * NV + t2) * 32, brow + t2 * G * 8);
+                        }
                 }
             }
             cp_async_commit();
@@ -468,7 +506,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
             cp_async_wait<1>();
             __syncwarp(g.mask);
             const int eb = tb0 + b * U;
-            const uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
+            const Vec* sl = wring + (b & 1) * U * NV * 32 + lane;
             const int o = (((b * U) / TG) & 1) * 128 + (b * U) % TG;
             int rc[U];
             float sc[U];
@@ -489,11 +527,8 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
 #pragma unroll
                     for (int t = 0; t < NV; ++t) {
                         if (!vin[t]) continue;
-                        const uint4 v = sl[(u * NV + t) * 32];
-                        Raw<DT, VECN> rb;
-                        rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
                         float bf[VECN];
-                        unpack_all<DT, VECN>(rb, bf);
+                        unpack_vec<DT, VECN>(sl[(u * NV + t) * 32], bf);
                         axpy_pairs<VECN>(acc[t], sc[u], bf);
                     }
             } else {
@@ -513,11 +548,8 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
 #pragma unroll
                     for (int t = 0; t < NV; ++t) {
                         if (!vin[t]) continue;
-                        const uint4 v = sl[(u * NV + t) * 32];
-                        Raw<DT, VECN> rb;
-                        rb.w[0] = v.x; rb.w[1] = v.y; rb.w[2] = v.z; rb.w[3] = v.w;
                         float bf[VECN];
-                        unpack_all<DT, VECN>(rb, bf);
+                        unpack_vec<DT, VECN>(sl[(u * NV + t) * 32], bf);
                         axpy_pairs<VECN>(acc[t], sc[u], bf);
                     }
                 }

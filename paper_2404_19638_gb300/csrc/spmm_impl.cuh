@@ -285,31 +285,31 @@ __global__ void __launch_bounds__(256, VECN > 1 ? (U * NV <= 4 ? 4 : (U * NV <= 
 
 // Ring path: one group per span of the balanced schedule, gathered rows
 // staged in the warp's shared-memory ring (ring.cuh).
-template <int DT, int G, int NV, int U>
-__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(NV, U))) k_spmm_ring(const SpmmArgs a)
+template <int DT, int G, int NV, int U, int VB>
+__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(NV, U, VB))) k_spmm_ring(const SpmmArgs a)
 {
     extern __shared__ __align__(16) unsigned char ring_smem[];
     const Group<G> g;
-    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (spmm_ring_bytes(NV, U) / 16);
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (spmm_ring_bytes(NV, U, VB) / 16);
     const int kb = blockIdx.y, nkb = gridDim.y;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const bool allv = a.K / vec_elems(DT) >= (kb + 1) * G * NV;
+    const bool allv = a.K / (VB / dt_bytes(DT)) >= (kb + 1) * G * NV;
     for (int64_t c = gid; c < a.nchunks; c += ngroups) {
         const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
         const int4 m = a.meta[c];
         if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
         const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-        if (allv) spmm_ring_span<DT, G, NV, U, true>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
-        else spmm_ring_span<DT, G, NV, U, false>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+        if (allv) spmm_ring_span<DT, G, NV, U, true, VB>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
+        else spmm_ring_span<DT, G, NV, U, false, VB>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
     }
 }
 
-template <int DT>
+template <int DT, int VB>
 inline const void* spmm_ring_kernel_for(int shape)
 {
     switch (shape) {
-#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm_ring<DT, G_, NV_, U_>;
+#define X(i, G_, NV_, U_) case i: return (const void*)&k_spmm_ring<DT, G_, NV_, U_, VB>;
         SPK_SHAPES(X)
 #undef X
     }
@@ -341,19 +341,26 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     if constexpr (DTB != DT_E4M3) {
         const bool ring_ok = L.vec && L.ring && a.bnd && !a.vperm && !a.vals2 && (!a.vals || a.vals_staged);
         if (ring_ok) {
-            const void* rf = spmm_ring_kernel_for<DTB>(L.shape);
+            // 16-bit operands whose 16-byte vectors would leave half the group's
+            // lanes idle are spread over all of them as 8-byte vectors
+            constexpr bool can_half = (DTB == DT_BF16 || DTB == DT_F16);
+            const bool half = can_half && 2 * nvec <= sh.G * sh.NV && a.K % 4 == 0;
+            const int vb = half ? 8 : 16;
+            const void* rf = half ? spmm_ring_kernel_for<DTB, (can_half ? 8 : 16)>(L.shape)
+                                  : spmm_ring_kernel_for<DTB, 16>(L.shape);
             if (!rf) return cudaErrorInvalidValue;
+            const int nkb2 = half ? (a.K / 4 + sh.G * sh.NV - 1) / (sh.G * sh.NV) : nkb;
             const int64_t groups_per_cta = RING_THREADS / sh.G;
             int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
             if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-            if (nkb > 65535) return cudaErrorInvalidValue;
-            const size_t smem = (size_t)(RING_THREADS / 32) * spmm_ring_bytes(sh.NV, sh.U);
+            if (nkb2 > 65535) return cudaErrorInvalidValue;
+            const size_t smem = (size_t)(RING_THREADS / 32) * spmm_ring_bytes(sh.NV, sh.U, vb);
             if (smem > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(rf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
             }
             void* args[] = {(void*)&a};
-            return cudaLaunchKernel(rf, dim3((unsigned)blocks, (unsigned)nkb), dim3(RING_THREADS), args, smem, s);
+            return cudaLaunchKernel(rf, dim3((unsigned)blocks, (unsigned)nkb2), dim3(RING_THREADS), args, smem, s);
         }
     }
     const int64_t groups_per_cta = L.threads / sh.G;

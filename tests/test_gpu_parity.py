@@ -279,3 +279,27 @@ def test_duplicates_are_independent_entries(spk):
     S = spk.CSR(rp, ci, (2, 2), torch.from_numpy(vals), device=DEV)
     C = spk.spmm(S, torch.from_numpy(B).to(DEV)).cpu().numpy()
     assert np.array_equal(C, oracle.spmm(rp, ci, B, vals))
+
+
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("K", [16, 32, 64, 128])
+def test_spmm_16bit_lane_layouts(spk, dt, K):
+    """16-bit SpMM: 16-byte lane vectors, or 8-byte vectors over twice the
+    lanes when a 16-byte layout would leave half the group idle; both give the
+    same bits as the register path (each output element accumulates its
+    nonzeros in the same order)."""
+    M, N = 500, 420
+    rp, ci, vals, A, B = _case(M, N, K, seed=K + 11, long_row=2500)
+    S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV, chunk_work=96)
+    tB = spk.cast(torch.from_numpy(B).to(DEV), dt)
+    fmt = "bf16" if dt == torch.bfloat16 else "f16"
+    Bq = tB.view(torch.int16).cpu().numpy().view(np.uint16)
+    ref = oracle.spmm(rp, ci, Bq, vals, fmt_b=fmt)
+    den = oracle.spmm(rp, ci, Bq, vals, fmt_b=fmt, absmode=True)
+    base = spk.spmm(S, tB, tune={"variant": 3}).cpu().numpy()
+    assert comp_err(base, ref, den) <= TOL
+    for shape in [(4, 1, 4), (8, 1, 4), (16, 1, 8), (32, 1, 8), (4, 2, 4), (8, 2, 4)]:
+        G, NV, U = shape
+        got = spk.spmm(S, tB, tune={"variant": 2, "group_lanes": G, "vecs_per_lane": NV, "unroll": U}).cpu().numpy()
+        assert np.array_equal(got, base), shape
+    assert np.array_equal(spk.spmm(S, tB).cpu().numpy(), base)
