@@ -261,6 +261,20 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------------------------
+# replicas: every rank times its own copy of the step; the job's time is the
+# slowest rank's
+# ----------------------------------------------------------------------------
+def max_over_ranks(x: float, device) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def event_ms(fn, stream, flush, reps=5):
@@ -408,10 +422,7 @@ def main(args):
     t_sd = [e[0].elapsed_time(e[1]) for e in events]
     t_sp = [e[1].elapsed_time(e[2]) for e in events]
     T = (sum(t_sd) + sum(t_sp)) / 1e3                      # seconds, this rank
-    if world > 1:
-        tt = torch.tensor([T], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        T = float(tt.item())
+    T = max_over_ranks(T, dev)
     flops_step = 2.0 * 2.0 * P.nnz * K
     value = world * flops_step * args.steps / T / 1e9
 
@@ -474,10 +485,7 @@ def main(args):
     e1.record(s_out)
     torch.cuda.synchronize(dev)
     Te = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([Te], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        Te = float(tt.item())
+    Te = max_over_ranks(Te, dev)
     h2d = (hA.numel() * 4 + (0 if hB is hA else hB.numel() * 4) + (0 if hv is None else hv.numel() * 4))
     d2h = hout.numel() * 4 + hC.numel() * 4
 
@@ -601,10 +609,7 @@ def main_batch(args):
     if world > 1:
         dist.barrier()
     T = sum(a.elapsed_time(b) for a, b in events) / 1e3
-    if world > 1:
-        tt = torch.tensor([T], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        T = float(tt.item())
+    T = max_over_ranks(T, dev)
     ms = 1e3 * T / args.steps
 
     # the same work as one launch per (matrix, op), for comparison
