@@ -708,7 +708,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn", "batch"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--chunk-work", type=int, default=512)
+    ap.add_argument("--chunk-work", type=int, default=None,
+                    help="balanced-schedule chunk size (default 512; 128 for the batched workload)")
     ap.add_argument("--tune-sddmm", default=None, help='JSON spk_tune fields, e.g. {"group_lanes": 8}')
     ap.add_argument("--tune-spmm", default=None)
     ap.add_argument("--cpu-nnz", type=int, default=2_000_000, help="nonzeros in the CPU-baseline sample")
@@ -718,6 +719,9 @@ def parse():
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
+    if a.chunk_work is None:
+        # many small matrices with short rows: smaller chunks keep more warps busy
+        a.chunk_work = 128 if a.workload == "batch" else 512
     return a
 
 
