@@ -49,14 +49,57 @@ class Batch:
                                K=K, out=it.out.data_ptr(), ldc=it.out.stride(0) if it.op == OP_SPMM else 0,
                                tune=None if t is None else ctypes.pointer(t))
         self._arr = arr
+        self._h = ctypes.c_void_p()
+        self._create()
+
+    def _create(self) -> None:
+        """(Re)build the native work list from the items' current schedules."""
+        self._destroy()
         nbytes = ctypes.c_size_t()
-        check(lib().spk_batch_size(arr, len(items), ctypes.byref(nbytes)), "spk_batch_size")
+        check(lib().spk_batch_size(self._arr, len(self.items), ctypes.byref(nbytes)), "spk_batch_size")
         self._storage = _buffer(nbytes.value, self.device)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(lib().spk_batch_create(arr, len(items), self._storage.data_ptr(), self._storage.numel(),
+            check(lib().spk_batch_create(self._arr, len(self.items), self._storage.data_ptr(), self._storage.numel(),
                                          ctypes.byref(self._h), _stream(self.device)), "spk_batch_create")
         self._graph = None
+
+    def _destroy(self) -> None:
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().spk_batch_destroy(h)
+        self._h = None
+
+    def autotune(self, chunk_works=(64, 128, 256, 512), reps: int = 3) -> dict:
+        """Pick the balanced-schedule chunk size of the whole batch by timing
+        one persistent launch per candidate (CUDA events, median of reps);
+        every item's schedule is rebuilt with the winner.  Returns
+        {"chunk_work": W, "ms": {W: median ms}}."""
+        patterns = []
+        for it in self.items:
+            if all(it.S is not p for p in patterns):
+                patterns.append(it.S)
+        times = {}
+        for W in chunk_works:
+            for S in patterns:
+                S.build_schedule(W)
+            self._create()
+            self.run()
+            torch.cuda.synchronize(self.device)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                self.run()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            times[W] = sorted(ts)[len(ts) // 2]
+        best = min(times, key=times.get)
+        for S in patterns:
+            S.build_schedule(best)
+        self._create()
+        return {"chunk_work": best, "ms": times}
 
     def info(self) -> dict:
         units, ctas = ctypes.c_int64(), ctypes.c_int32()
@@ -82,13 +125,10 @@ class Batch:
         self.capture().replay()
 
     def __del__(self):
-        h = getattr(self, "_h", None)
-        if h is not None and h.value:
-            try:
-                lib().spk_batch_destroy(h)
-            except Exception:
-                pass
-            self._h = None
+        try:
+            self._destroy()
+        except Exception:
+            pass
 
 
 __all__ = ["Batch", "Item", "OP_SDDMM", "OP_SPMM"]

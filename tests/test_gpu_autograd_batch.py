@@ -163,3 +163,25 @@ def test_batch_graph_replay(spk):
     for (S, A, B), o, p in zip(keep, outs, probs):
         ref = oracle.spmm(p.rowptr, p.colidx, p.B, p.vals)
         assert comp_err(o.cpu().numpy(), ref, oracle.spmm(p.rowptr, p.colidx, p.B, p.vals, absmode=True)) <= TOL
+
+
+def test_batch_autotune_keeps_results(spk):
+    probs = _batch_problems(10, seed=21)
+    items, keep = [], []
+    for k, p in enumerate(probs):
+        S = spk.CSR(p.rowptr, p.colidx, (p.M, p.N), torch.from_numpy(p.vals), device=DEV, chunk_work=512)
+        B = torch.from_numpy(p.B).to(DEV)
+        out = torch.full((p.M, p.K), float("nan"), device=DEV)
+        items.append(spk.Item(spk.OP_SPMM, S, B, out))
+        keep.append((S, B, out, p))
+    batch = spk.Batch(items)
+    res = batch.autotune((64, 256), reps=2)
+    assert res["chunk_work"] in (64, 256) and set(res["ms"]) == {64, 256}
+    for S, B, out, p in keep:
+        assert S.schedule_info()["chunk_work"] == res["chunk_work"]
+        out.fill_(float("nan"))
+    batch.run()
+    torch.cuda.synchronize()
+    for S, B, out, p in keep:
+        ref = oracle.spmm(p.rowptr, p.colidx, p.B, p.vals)
+        assert comp_err(out.cpu().numpy(), ref, oracle.spmm(p.rowptr, p.colidx, p.B, p.vals, absmode=True)) <= TOL
