@@ -105,7 +105,7 @@ spk_status spk_csr_destroy(spk_csr S);
  * the kernel fills: {first error code (0 = valid), first bad index, number of
  * bad entries, 1 if some row has unsorted or repeated columns}.  The caller
  * reads it after synchronising `stream`.  Returns SPK_OK if the check was
- * launched; the verdict is in d_report. */
+ * launched; the outcome is in d_report. */
 spk_status spk_csr_validate(spk_csr S, int32_t* d_report, void* stream);
 
 /* ------------------------------------------------------------ schedule -- */

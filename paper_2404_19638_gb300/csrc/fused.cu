@@ -692,11 +692,12 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
             }
             float ev[U];
             if (eb >= e0 && eb + U <= e1 && rc[U - 1] == cur && cur == acur) {
-                float bf[U][VECN];
 #pragma unroll
-                for (int u = 0; u < U; ++u) unpack_v(sl[u * 32], bf[u]);
-#pragma unroll
-                for (int u = 0; u < U; ++u) ev[u] = dot(bf[u]);
+                for (int u = 0; u < U; ++u) {
+                    float bf[VECN];
+                    unpack_v(sl[u * 32], bf);
+                    ev[u] = dot(bf);
+                }
                 head_allreduce<G, U>(g, NH, ev);
 #pragma unroll
                 for (int u = 0; u < U; ++u) ev[u] = scale * (sc[u] * ev[u]);
@@ -712,25 +713,31 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                     for (int u = 0; u < U; ++u) {
                         const float w = expf(ev[u] - mb);
                         l += w;
-                        axpy_pairs<VECN>(acc, w, bf[u]);
+                        float bf[VECN];
+                        unpack_v(sl[u * 32], bf);           // re-read: keeps U rows out of registers
+                        axpy_pairs<VECN>(acc, w, bf);
                     }
                     m = mb;
                 } else {
 #pragma unroll
-                    for (int u = 0; u < U; ++u) axpy_pairs<VECN>(acc, ev[u], bf[u]);
+                    for (int u = 0; u < U; ++u) {
+                        float bf[VECN];
+                        unpack_v(sl[u * 32], bf);
+                        axpy_pairs<VECN>(acc, ev[u], bf);
+                    }
                 }
             } else {
                 // span edge or row change: all U dots first (the A slice switches
                 // where a new row starts), one reduction for the batch, then the
                 // rows are closed and accumulated in order
-                float bf[U][VECN];
                 bool first = true;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     ev[u] = 0.f;
                     const int e = eb + u;
                     if (e < e0 || e >= e1) continue;
-                    unpack_v(sl[u * 32], bf[u]);
+                    float bfu[VECN];
+                    unpack_v(sl[u * 32], bfu);
                     if (rc[u] != acur) {
                         if (first) unpack_v(ringA[(b & 1) * 32 + lane], av);
                         else load_elems<DT, VECN>(reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)rc[u] * lda_bytes,
@@ -738,7 +745,7 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                         first = false;
                         acur = rc[u];
                     }
-                    ev[u] = dot(bf[u]);
+                    ev[u] = dot(bfu);
                 }
                 head_allreduce<G, U>(g, NH, ev);
 #pragma unroll
@@ -755,6 +762,8 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                         m = -INFINITY;
                         l = 0.f;
                     }
+                    float bf[VECN];
+                    unpack_v(sl[u * 32], bf);
                     if (smax) {
                         const float mb = fmaxf(m, ev[u]);
                         const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
@@ -762,10 +771,10 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                         for (int q = 0; q < VECN; ++q) acc[q] *= c;
                         const float w = expf(ev[u] - mb);
                         l = l * c + w;
-                        axpy_pairs<VECN>(acc, w, bf[u]);
+                        axpy_pairs<VECN>(acc, w, bf);
                         m = mb;
                     } else {
-                        axpy_pairs<VECN>(acc, ev[u], bf[u]);
+                        axpy_pairs<VECN>(acc, ev[u], bf);
                     }
                 }
             }
@@ -808,17 +817,19 @@ static cudaError_t launch_fused_mh_t(int G, const FusedArgs& a, cudaStream_t s)
 {
     const void* fn = nullptr;
     switch (G) {
+    // 4 nonzeros a batch (8 measured slower: more registers, fewer warps)
     case 4: fn = (const void*)&k_fused_mh<DT, 4, 4>; break;
     case 8: fn = (const void*)&k_fused_mh<DT, 8, 4>; break;
     case 16: fn = (const void*)&k_fused_mh<DT, 16, 4>; break;
     case 32: fn = (const void*)&k_fused_mh<DT, 32, 4>; break;
     default: return cudaErrorInvalidValue;
     }
+    constexpr int U = 4;
     if (a.nchunks <= 0) return cudaSuccess;
     const int64_t groups_per_cta = RING_THREADS / G;
     int64_t blocks = (a.nchunks + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    const size_t smem = (size_t)(RING_THREADS / 32) * fused_mh_ring_bytes(4);
+    const size_t smem = (size_t)(RING_THREADS / 32) * fused_mh_ring_bytes(U);
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3((unsigned)blocks, 1), dim3(RING_THREADS), args, smem, s);
 }
