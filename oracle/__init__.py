@@ -301,3 +301,35 @@ def gnn_grad(rowptr, colidx, H, dY, vals=None, fmt=None):
     g2 = spmm_t(rowptr, colidx, N, H, vals, dE, fmt_y=fmt)
     g3 = spmm_t(rowptr, colidx, N, dY, e)
     return g1 + g2 + g3
+
+
+def fusedmm_grad(rowptr, colidx, A, B, dY, vals=None, *, heads=1, scale=1.0, softmax=False, fmt=None):
+    """dA, dB of L = sum dY . Y for Y = fusedmm(S, A, B) (Sec. 2's SDDMM -> SpMM
+    cascade), by the chain rule per head h over columns h*K/heads.. :
+      e = scale s <a_i, b_j>,  w = e or softmax_j(e),  Y_i = sum_j w_ij b_j
+      dw_ij = <dY_i, b_j>;  g = dw, or w (dw - sum_j' w_ij' dw_ij') with softmax
+      c = scale g;  dA = (S.c) B;  dB = (S.c)^T A + W^T dY.
+    The weights come from this oracle's own FusedMM forward (scores, lse)."""
+    rowptr = _c(rowptr, np.int32); colidx = _c(colidx, np.int32)
+    M, K = A.shape
+    N = B.shape[0]
+    Kh = K // heads
+    rows = np.repeat(np.arange(M), np.diff(rowptr))
+    dY = np.asarray(dY, np.float64)
+    _, scores, lse = fusedmm(rowptr, colidx, A, B, vals, heads=heads, scale=scale, softmax=softmax,
+                             fmt_a=fmt, fmt_b=fmt)
+    dA = np.zeros((M, K))
+    dB = np.zeros((N, K))
+    for h in range(heads):
+        sl = slice(h * Kh, (h + 1) * Kh)
+        w = np.exp(scores[h] - lse[rows, h]) if softmax else scores[h]
+        dw = sddmm(rowptr, colidx, dY[:, sl], B[:, sl], None, None, fmt_b=fmt)
+        if softmax:
+            rowsum = np.bincount(rows, weights=w * dw, minlength=M)
+            g = w * (dw - rowsum[rows])
+        else:
+            g = dw
+        c = scale * g
+        dA[:, sl] = spmm(rowptr, colidx, B[:, sl], vals, c, fmt_b=fmt)
+        dB[:, sl] = spmm_t(rowptr, colidx, N, A[:, sl], vals, c, fmt_y=fmt) + spmm_t(rowptr, colidx, N, dY[:, sl], w)
+    return dA, dB

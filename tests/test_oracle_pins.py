@@ -461,3 +461,43 @@ def test_fusedmm_plain_is_spmm_of_scores_and_absmode():
         np.testing.assert_allclose(Yabs[:, sl], dense(rp, ci, ab, M, N) @ np.abs(B[:, sl].astype(np.float64)),
                                    rtol=1e-12, atol=1e-12)
     assert np.all(Yabs >= np.abs(Y) - 1e-12)
+
+
+@pytest.mark.parametrize("heads,softmax", [(1, False), (2, True), (3, True), (3, False)])
+def test_fusedmm_gradient_fd(heads, softmax):
+    """The FusedMM backward's chain rule against central finite differences
+    of the oracle's own forward (a dropped softmax row term, a missing W^T dY
+    contribution or a wrong head slice moves the directional derivative)."""
+    M, N, K = 14, 11, 6 * heads
+    rp, ci, vals, A, B = random_case(M, N, K, 0.35, seed=40 + heads)
+    A = A.astype(np.float64) * 0.5; B = B.astype(np.float64) * 0.5; vals = vals.astype(np.float64)
+    g = np.random.default_rng(41)
+    dY = g.standard_normal((M, K))
+    kw = dict(heads=heads, scale=0.8, softmax=softmax)
+    dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, **kw)
+    L = lambda A_, B_: (dY * oracle.fusedmm(rp, ci, A_, B_, vals, **kw)[0]).sum()
+    for _ in range(3):
+        VA, VB = g.standard_normal(A.shape), g.standard_normal(B.shape)
+        fa, fb = _fd(lambda t: L(t, B), A, VA), _fd(lambda t: L(A, t), B, VB)
+        assert abs(fa - (dA * VA).sum()) <= 1e-6 * max(1.0, abs(fa))
+        assert abs(fb - (dB * VB).sum()) <= 1e-6 * max(1.0, abs(fb))
+    # rows with no entries get no gradient in A
+    empty = np.flatnonzero(np.diff(rp) == 0)
+    assert empty.size and np.all(dA[empty] == 0.0)
+
+
+def test_fusedmm_gradient_softmax_rows_sum_to_zero_in_scores():
+    """With softmax, a shift of every score in a row leaves Y unchanged: the
+    score gradient of each row sums to zero, i.e. for A = B = 0 directions
+    that only shift scores the derivative vanishes (checked through dA along
+    a_i itself when all b_j in the row are equal)."""
+    M, N, K = 4, 5, 3
+    rp = np.array([0, 3, 3, 5, 7], np.int32)
+    ci = np.array([0, 2, 4, 1, 3, 0, 4], np.int32)
+    A = np.random.default_rng(3).standard_normal((M, K))
+    B = np.tile(np.array([[0.3, -0.2, 0.5]]), (N, 1))      # all b_j equal
+    dY = np.random.default_rng(4).standard_normal((M, K))
+    dA, _ = oracle.fusedmm_grad(rp, ci, A, B, dY, softmax=True)
+    # scores in a row are equal, weights uniform, and a change of a_i shifts
+    # every score of the row by the same amount: Y does not move
+    np.testing.assert_allclose(dA, 0.0, atol=1e-14)
