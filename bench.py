@@ -346,9 +346,21 @@ def aux_measurements(spk, S, P, A32, A, B, dt, elt, flush, stream, args):
         t = event_ms(lambda: spk.fusedmm(S, A, Bd, out=Yl, **kw), stream, flush)
         out[name] = t
         out[name.replace("_ms", "_algo_gbs")] = fb / (t / 1e3) / 1e9
+    if "fusedmm_softmax_4heads_ms" in out:
+        # forward + backward of the differentiable layer (dA and dB, 4 heads, softmax)
+        Ag = A.detach().clone().requires_grad_()
+        Bg = Bd.detach().clone().requires_grad_()
+        dY = torch.ones((P.M, P.K), dtype=torch.float32, device=dev)
+
+        def fwd_bwd():
+            Ag.grad = None
+            Bg.grad = None
+            spk.autograd.fusedmm(S, Ag, Bg, S.vals, heads=4, softmax=True).backward(dY)
+        out["fusedmm_softmax_4heads_fwd_bwd_ms"] = event_ms(fwd_bwd, stream, flush)
+        del Ag, Bg, dY
     out["note"] = ("measured after the timed step on the same pattern; builds by wall clock, kernels by CUDA "
                    "events with the L2 flushed; layer_separate = SDDMM then SpMM on its scores, fusedmm = the "
-                   "same layer in one kernel")
+                   "same layer in one kernel; fwd_bwd = that layer differentiated (forward, then dA and dB)")
     return out
 
 

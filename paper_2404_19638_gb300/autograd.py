@@ -119,4 +119,69 @@ def gnn_layer(S: CSR, H, vals=None):
     return GNNLayerFunction.apply(S, vals, H)
 
 
-__all__ = ["SDDMMFunction", "SpMMFunction", "GNNLayerFunction", "sddmm", "spmm", "gnn_layer"]
+class FusedMMFunction(torch.autograd.Function):
+    """Differentiable FusedMM: per head h, e = scale * s * <A_i, B_j>,
+    w = e or its row softmax, Y_i = sum_j w_ij B_j.
+
+    Backward (chain rule, per head; dw_ij = <dY_i, B_j>):
+      g = dw, or w * (dw - rowdot_i) with softmax, rowdot_i = sum_j w_ij dw_ij
+          = <dY_i, Y_i> (read from the saved output)
+      c = scale * g;  dA = (S.c) B;  dB = (S.c)^T A + W^T dY
+    Steps: one SDDMM per head for dw, the row term and score gradient
+    kernels, then SpMM / SpMM^T per head accumulating in FP32.  The sparse
+    values are not differentiated.
+    """
+
+    @staticmethod
+    def forward(ctx, S: CSR, vals, A, B, heads: int, scale: float, softmax: bool):
+        v = _vals_or_none(vals)
+        Y, scores, lse = ops.fusedmm(S, A, B, v, heads=heads, scale=scale, softmax=softmax, want_scores=True,
+                                     want_lse=softmax, use_default_vals=False)
+        ctx.S, ctx.heads, ctx.scale, ctx.softmax = S, heads, scale, softmax
+        ctx.save_for_backward(vals, A, B, Y, scores, lse if softmax else scores[:0])
+        return Y
+
+    @staticmethod
+    def backward(ctx, dY):
+        vals, A, B, Y, scores, lse = ctx.saved_tensors
+        S, heads, scale, softmax = ctx.S, ctx.heads, ctx.scale, ctx.softmax
+        dY = dY.contiguous().float()
+        v = _vals_or_none(vals)
+        K = A.size(1)
+        Kh = K // heads
+        w = ops.fused_weights(S, scores, lse, heads, softmax) if softmax else scores
+        dw = torch.empty_like(scores)
+        for h in range(heads):
+            c0 = h * Kh
+            ops.sddmm(S, dY[:, c0:c0 + Kh], B[:, c0:c0 + Kh], out=dw[h], use_default_vals=False)
+        R = ops.fused_rowdot(dY, Y, heads) if softmax else None
+        c = ops.fused_score_grad(S, w, dw, R, heads, softmax, scale)
+        dA = dB = None
+        if ctx.needs_input_grad[2]:
+            dA = torch.empty((S.M, K), dtype=torch.float32, device=S.device)
+            for h in range(heads):
+                c0 = h * Kh
+                ops.spmm(S, B[:, c0:c0 + Kh], v, c[h], out=dA[:, c0:c0 + Kh], use_default_vals=False)
+            if A.dtype != torch.float32:
+                dA = ops.cast(dA, A.dtype)
+        if ctx.needs_input_grad[3]:
+            dB = torch.empty((S.N, K), dtype=torch.float32, device=S.device)
+            for h in range(heads):
+                c0 = h * Kh
+                ops.spmm_t(S, A[:, c0:c0 + Kh], v, c[h], out=dB[:, c0:c0 + Kh], use_default_vals=False)
+                ops.spmm_t(S, dY[:, c0:c0 + Kh], w[h], out=dB[:, c0:c0 + Kh], accumulate=True,
+                           use_default_vals=False)
+            if B.dtype != torch.float32:
+                dB = ops.cast(dB, B.dtype)
+        return None, None, dA, dB, None, None, None
+
+
+def fusedmm(S: CSR, A, B, vals=None, *, heads: int = 1, scale: float = 1.0, softmax: bool = False):
+    """Differentiable FusedMM (FP32 output M x K); ``vals`` None means all ones."""
+    if vals is None:
+        vals = torch.empty(0, dtype=torch.float32, device=S.device)
+    return FusedMMFunction.apply(S, vals, A, B, int(heads), float(scale), bool(softmax))
+
+
+__all__ = ["SDDMMFunction", "SpMMFunction", "GNNLayerFunction", "FusedMMFunction", "sddmm", "spmm", "gnn_layer",
+           "fusedmm"]

@@ -488,6 +488,42 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     return SPK_OK;
 }
 
+extern "C" spk_status spk_fused_weights(spk_csr S, int32_t heads, int32_t softmax, const float* scores,
+                                        const float* lse, float* w, void* stream)
+{
+    REQUIRE(S && heads >= 1 && (softmax == 0 || softmax == 1), SPK_ERR_ARG, "spk_fused_weights: bad argument");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_fused_weights: needs spk_schedule_build first");
+    REQUIRE(S->nnz == 0 || (scores && w && (!softmax || lse)), SPK_ERR_ARG, "spk_fused_weights: NULL array");
+    cudaError_t e = launch_fused_weights(S->rowidx, S->nnz, heads, softmax, scores, lse, w, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_fused_weights");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* dY, int64_t lddy,
+                                       const float* Y, int64_t ldy, float* rowdot, void* stream)
+{
+    REQUIRE(M >= 0 && K >= 1 && heads >= 1 && K % heads == 0, SPK_ERR_SHAPE,
+            "spk_fused_rowdot: need M >= 0 and K a positive multiple of heads");
+    REQUIRE(M == 0 || (dY && Y && rowdot), SPK_ERR_ARG, "spk_fused_rowdot: NULL array");
+    REQUIRE(M <= 1 || (lddy >= K && ldy >= K), SPK_ERR_SHAPE, "spk_fused_rowdot: row strides below K");
+    cudaError_t e = launch_fused_rowdot(M, K, heads, dY, lddy, Y, ldy, rowdot, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_fused_rowdot");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* w,
+                                           const float* dw, const float* rowdot, float* de, void* stream)
+{
+    REQUIRE(S && heads >= 1 && (softmax == 0 || softmax == 1), SPK_ERR_ARG, "spk_fused_score_grad: bad argument");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_fused_score_grad: needs spk_schedule_build first");
+    REQUIRE(S->nnz == 0 || (dw && de && (!softmax || (w && rowdot))), SPK_ERR_ARG,
+            "spk_fused_score_grad: NULL array");
+    cudaError_t e = launch_fused_score_grad(S->rowidx, S->nnz, heads, softmax, scale, w, dw, rowdot, de,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_fused_score_grad");
+    return SPK_OK;
+}
+
 // ----------------------------------------------------------------------------
 // SpMM with library-held scratch
 // ----------------------------------------------------------------------------

@@ -403,6 +403,12 @@ struct TplanLayout {
 TplanLayout tplan_layout(int64_t M, int64_t N, int64_t nnz, int32_t W);
 cudaError_t launch_fused(int dt, const Launch& L, const FusedArgs& a, cudaStream_t s);
 cudaError_t launch_fused_mh(int dt, int G, const FusedArgs& a, cudaStream_t s);
+cudaError_t launch_fused_weights(const int32_t* rowidx, int64_t nnz, int heads, int softmax, const float* scores,
+                                 const float* lse, float* w, cudaStream_t s);
+cudaError_t launch_fused_rowdot(int64_t M, int K, int heads, const float* dY, int64_t lddy, const float* Y,
+                                int64_t ldy, float* rowdot, cudaStream_t s);
+cudaError_t launch_fused_score_grad(const int32_t* rowidx, int64_t nnz, int heads, int softmax, float scale,
+                                    const float* w, const float* dw, const float* rowdot, float* de, cudaStream_t s);
 int fused_shape_index(int G, int NV, int U);   // -1 if not compiled
 cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const float* vals2, int64_t nnz, float* out,
                                 cudaStream_t s);

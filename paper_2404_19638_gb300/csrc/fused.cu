@@ -869,6 +869,91 @@ static cudaError_t launch_fused_t(const Launch& L, const FusedArgs& a, cudaStrea
     return cudaLaunchKernel(fn, dim3((unsigned)blocks, (unsigned)a.heads), dim3(RING_THREADS), args, smem, s);
 }
 
+// ----------------------------------------------------------------------------
+// Elementwise steps of the FusedMM backward, per head h and stored entry e of
+// row i (COO row from the schedule):
+//   weights:    w = e_h, or exp(e_h - lse[i, h]) with softmax
+//   score grad: de = scale * dw, or scale * w * (dw - rowdot[i, h]) with softmax
+// ----------------------------------------------------------------------------
+__global__ void k_fused_weights(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t heads, int32_t softmax,
+                                const float* __restrict__ scores, const float* __restrict__ lse, float* __restrict__ w)
+{
+    const int64_t n = nnz * heads;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = q / nnz, e = q - h * nnz;
+        const float sc = scores[q];
+        w[q] = softmax ? expf(sc - __ldg(lse + (int64_t)__ldg(rowidx + e) * heads + h)) : sc;
+    }
+}
+
+__global__ void k_fused_score_grad(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t heads, int32_t softmax,
+                                   float scale, const float* __restrict__ w, const float* __restrict__ dw,
+                                   const float* __restrict__ rowdot, float* __restrict__ de)
+{
+    const int64_t n = nnz * heads;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t h = q / nnz, e = q - h * nnz;
+        float g = dw[q];
+        if (softmax) g = w[q] * (g - __ldg(rowdot + (int64_t)__ldg(rowidx + e) * heads + h));
+        de[q] = scale * g;
+    }
+}
+
+// rowdot[i, h] = <dY[i, head h], Y[i, head h]>: with Y[i, h] = sum_j w_ij B[j, h]
+// this equals sum_j w_ij <dY_i, B_j> = sum_j w_ij dw_ij, the softmax
+// backward's row term, read from two dense rows instead of a sparse row
+// (balanced whatever the degree).  One warp per row.
+__global__ void k_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* __restrict__ dY, int64_t lddy,
+                               const float* __restrict__ Y, int64_t ldy, float* __restrict__ rowdot)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int Kh = K / heads;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M; i += warps) {
+        const float* g = dY + i * lddy;
+        const float* y = Y + i * ldy;
+        for (int h = 0; h < heads; ++h) {
+            float acc = 0.f;
+            for (int c = h * Kh + lane; c < (h + 1) * Kh; c += 32) acc = fmaf(__ldg(g + c), __ldg(y + c), acc);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) rowdot[i * heads + h] = acc;
+        }
+    }
+}
+
+cudaError_t launch_fused_rowdot(int64_t M, int K, int heads, const float* dY, int64_t lddy, const float* Y,
+                                int64_t ldy, float* rowdot, cudaStream_t s)
+{
+    if (M <= 0) return cudaSuccess;
+    int64_t blocks = (M + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_fused_rowdot<<<(unsigned)blocks, 256, 0, s>>>(M, K, heads, dY, lddy, Y, ldy, rowdot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_weights(const int32_t* rowidx, int64_t nnz, int heads, int softmax, const float* scores,
+                                 const float* lse, float* w, cudaStream_t s)
+{
+    const int64_t n = nnz * heads;
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_fused_weights<<<(unsigned)blocks, 256, 0, s>>>(rowidx, nnz, heads, softmax, scores, lse, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_score_grad(const int32_t* rowidx, int64_t nnz, int heads, int softmax, float scale,
+                                    const float* w, const float* dw, const float* rowdot, float* de, cudaStream_t s)
+{
+    const int64_t n = nnz * heads;
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_fused_score_grad<<<(unsigned)blocks, 256, 0, s>>>(rowidx, nnz, heads, softmax, scale, w, dw, rowdot, de);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fused(int dt, const Launch& L, const FusedArgs& a, cudaStream_t s)
 {
     switch (dt) {

@@ -160,6 +160,50 @@ def fusedmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, *, heads: int =
     return out, scores, lse
 
 
+def fused_weights(S: CSR, scores: torch.Tensor, lse, heads: int, softmax: bool) -> torch.Tensor:
+    """Per-entry weights of a FusedMM forward: the scores, or exp(score - lse[row])
+    with softmax.  heads x nnz FP32."""
+    if scores.shape != (heads, S.nnz) or scores.dtype != torch.float32:
+        raise ValueError("scores must be heads x nnz float32")
+    if softmax and (lse is None or lse.shape != (S.M, heads) or lse.dtype != torch.float32):
+        raise ValueError("softmax weights need lse (M x heads float32)")
+    w = torch.empty_like(scores)
+    check(lib().spk_fused_weights(S.handle, int(heads), int(bool(softmax)), scores.contiguous().data_ptr(),
+                                  _ptr(lse.contiguous() if softmax else None), w.data_ptr(), _stream(S.device)),
+          "spk_fused_weights")
+    return w
+
+
+def fused_rowdot(dY: torch.Tensor, Y: torch.Tensor, heads: int) -> torch.Tensor:
+    """rowdot[i, h] = <dY_i, Y_i> over head h's columns.  M x heads FP32."""
+    if dY.dtype != torch.float32 or Y.dtype != torch.float32 or dY.shape != Y.shape or dY.dim() != 2:
+        raise ValueError("dY and Y must be M x K float32 of one shape")
+    _, lddy = _dense(dY, "dY", dY.device)
+    _, ldy = _dense(Y, "Y", dY.device)
+    M, K = Y.shape
+    R = torch.empty((M, heads), dtype=torch.float32, device=Y.device)
+    check(lib().spk_fused_rowdot(M, K, int(heads), dY.data_ptr(), lddy, Y.data_ptr(), ldy, R.data_ptr(),
+                                 _stream(Y.device)), "spk_fused_rowdot")
+    return R
+
+
+def fused_score_grad(S: CSR, w: torch.Tensor, dw: torch.Tensor, rowdot, heads: int, softmax: bool,
+                     scale: float) -> torch.Tensor:
+    """Gradient w.r.t. the scaled dot products: scale * dw, or
+    scale * w * (dw - rowdot[row]) with softmax.  heads x nnz FP32."""
+    for t, name in ((w, "w"), (dw, "dw")):
+        if t.shape != (heads, S.nnz) or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be heads x nnz float32")
+    if softmax and (rowdot is None or rowdot.shape != (S.M, heads)):
+        raise ValueError("softmax score gradient needs rowdot (M x heads float32)")
+    de = torch.empty_like(dw)
+    check(lib().spk_fused_score_grad(S.handle, int(heads), int(bool(softmax)), float(scale),
+                                     w.contiguous().data_ptr(), dw.contiguous().data_ptr(),
+                                     _ptr(rowdot.contiguous() if softmax else None), de.data_ptr(),
+                                     _stream(S.device)), "spk_fused_score_grad")
+    return de
+
+
 def cast(x: torch.Tensor, dtype) -> torch.Tensor:
     """Round-to-nearest-even cast of an FP32 tensor to bfloat16 / float16."""
     if x.dtype != torch.float32 or not x.is_cuda:
@@ -185,4 +229,5 @@ def quantize_e4m3_rows(X: torch.Tensor):
     return Q, scales
 
 
-__all__ = ["sddmm", "spmm", "spmm_t", "cast", "quantize_e4m3_rows"]
+__all__ = ["sddmm", "spmm", "spmm_t", "fusedmm", "fused_weights", "fused_rowdot", "fused_score_grad", "cast",
+           "quantize_e4m3_rows"]

@@ -121,3 +121,16 @@ def test_python_binding_raises_with_message(L):
     with pytest.raises(SpkError) as ei:
         check(L.spk_csr_create(ctypes.byref(h), -3, 1, 0, 4096, None), "spk_csr_create")
     assert ei.value.code == "SPK_ERR_ARG" and "negative" in str(ei.value)
+
+
+def test_fused_backward_steps_reject_bad_arguments(L):
+    h = _handle(L)
+    assert L.spk_fused_weights(h, 2, 1, 4096, 8192, 12288, None) == 9        # no schedule: needs the COO rows
+    assert L.spk_fused_weights(h, 0, 0, 4096, None, 12288, None) == 1        # heads < 1
+    assert L.spk_fused_weights(h, 1, 2, 4096, None, 12288, None) == 1        # softmax flag not 0/1
+    assert L.spk_fused_score_grad(h, 2, 1, 1.0, 4096, 8192, 12288, 16384, None) == 9
+    assert L.spk_fused_rowdot(10, 12, 5, 4096, 12, 8192, 12, 12288, None) == 2   # K not a multiple of heads
+    assert L.spk_fused_rowdot(10, 12, 3, 4096, 8, 8192, 12, 12288, None) == 2    # row stride below K
+    assert L.spk_fused_rowdot(10, 12, 3, None, 12, 8192, 12, 12288, None) == 1
+    assert L.spk_fused_rowdot(0, 12, 3, None, 12, None, 12, None, None) == 0     # empty: nothing to do
+    L.spk_csr_destroy(h)

@@ -1,0 +1,158 @@
+"""Differentiable FusedMM on the GPU against the oracle's finite-difference
+pinned chain rule: the three elementwise kernels of the backward one by one
+(componentwise, FP32 tolerance), then dA and dB end to end for FP32 and BF16
+factors, with and without the row softmax, one and several heads."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TOL, comp_err, edge_pattern, row_of
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+# End-to-end gradients: FP32 throughout.  Each entry of dA / dB is a sum over
+# a row (or column) of products whose factors (scores, weights, dw, the row
+# term) each carry a few FP32 roundings relative to their magnitudes.  With
+# softmax the score gradients of a row sum to zero, so entries can cancel far
+# below the magnitudes of their terms: the check is normwise over the matrix,
+# max |got - ref| <= GRAD_TOL * max |ref|, where GRAD_TOL = 1e-4 leaves a
+# decade over rows of up to 2,500 terms while any dropped or mis-signed term
+# moves the result at the 1e-1 level.
+GRAD_TOL = 1e-4
+GRAD_TOL_16 = 2.0 ** -8 + GRAD_TOL     # plus one BF16 rounding of dA, dB
+
+
+@pytest.fixture(scope="module")
+def spk():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2404_19638_gb300 as m
+    return m
+
+
+def _case(M, N, K, seed, long_row=2500):
+    rp, ci = edge_pattern(M, N, seed, long_row=long_row)
+    g = np.random.default_rng(seed)
+    vals = g.uniform(0.5, 1.5, ci.size).astype(np.float32)
+    A = (0.5 * g.standard_normal((M, K))).astype(np.float32)
+    B = (0.5 * g.standard_normal((N, K))).astype(np.float32)
+    dY = g.standard_normal((M, K)).astype(np.float32)
+    return rp, ci, vals, A, B, dY
+
+
+def _normwise(got, ref):
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(np.asarray(got, np.float64) - ref)) / max(np.max(np.abs(ref)), 1e-300))
+
+
+def test_weights_kernel(spk):
+    rp, ci, vals, A, B, _ = _case(500, 400, 24, seed=1)
+    S = spk.CSR(rp, ci, (500, 400), device=DEV)
+    _, sc, lse = oracle.fusedmm(rp, ci, A, B, vals, heads=3, scale=0.5, softmax=True)
+    sc32, lse32 = sc.astype(np.float32), lse.astype(np.float32)
+    w = spk.ops.fused_weights(S, torch.from_numpy(sc32).to(DEV), torch.from_numpy(lse32).to(DEV), 3, True)
+    rows = row_of(rp)
+    ref = np.exp(sc32.astype(np.float64) - lse32.astype(np.float64)[rows].T)
+    # exp of an exactly representable FP32 difference: a few ulps of the result
+    # plus one rounding of the difference, scaled by the exponent's argument
+    den = ref * (1.0 + np.abs(sc32.astype(np.float64) - lse32.astype(np.float64)[rows].T))
+    assert comp_err(w.cpu().numpy(), ref, den) <= TOL
+    # without softmax the weights are the scores themselves
+    w0 = spk.ops.fused_weights(S, torch.from_numpy(sc32).to(DEV), None, 3, False)
+    assert np.array_equal(w0.cpu().numpy(), sc32)
+
+
+def test_rowdot_kernel(spk):
+    g = np.random.default_rng(2)
+    for (M, K, heads) in [(1, 4, 1), (333, 96, 3), (1000, 64, 4), (77, 40, 5)]:
+        dY = g.standard_normal((M, K)).astype(np.float32)
+        Y = g.standard_normal((M, K)).astype(np.float32)
+        R = spk.ops.fused_rowdot(torch.from_numpy(dY).to(DEV), torch.from_numpy(Y).to(DEV), heads).cpu().numpy()
+        Kh = K // heads
+        p = dY.astype(np.float64) * Y.astype(np.float64)
+        ref = p.reshape(M, heads, Kh).sum(axis=2)
+        den = np.abs(p).reshape(M, heads, Kh).sum(axis=2)
+        assert comp_err(R, ref, den) <= TOL
+    # a strided dY (a column block of a wider tensor)
+    W = torch.from_numpy(g.standard_normal((50, 64)).astype(np.float32)).to(DEV)
+    Y = torch.from_numpy(g.standard_normal((50, 32)).astype(np.float32)).to(DEV)
+    R = spk.ops.fused_rowdot(W[:, 16:48], Y, 2).cpu().numpy()
+    p = W[:, 16:48].double().cpu().numpy() * Y.double().cpu().numpy()
+    assert comp_err(R, p.reshape(50, 2, 16).sum(2), np.abs(p).reshape(50, 2, 16).sum(2)) <= TOL
+    # M = 0 is a no-op
+    E = torch.empty((0, 8), device=DEV)
+    assert spk.ops.fused_rowdot(E, E, 2).shape == (0, 2)
+
+
+@pytest.mark.parametrize("softmax", [False, True])
+def test_score_grad_kernel(spk, softmax):
+    rp, ci, _, _, _, _ = _case(400, 300, 8, seed=3)
+    S = spk.CSR(rp, ci, (400, 300), device=DEV)
+    g = np.random.default_rng(4)
+    heads, nnz = 2, ci.size
+    w = g.uniform(0, 1, (heads, nnz)).astype(np.float32)
+    dw = g.standard_normal((heads, nnz)).astype(np.float32)
+    R = g.standard_normal((400, heads)).astype(np.float32)
+    de = spk.ops.fused_score_grad(S, torch.from_numpy(w).to(DEV), torch.from_numpy(dw).to(DEV),
+                                  torch.from_numpy(R).to(DEV), heads, softmax, 0.3).cpu().numpy()
+    rows = row_of(rp)
+    w64, dw64, R64 = w.astype(np.float64), dw.astype(np.float64), R.astype(np.float64)[rows].T
+    if softmax:
+        ref = 0.3 * w64 * (dw64 - R64)
+        den = 0.3 * w64 * (np.abs(dw64) + np.abs(R64))
+    else:
+        ref = 0.3 * dw64
+        den = np.abs(ref)
+    assert comp_err(de, ref, den) <= TOL
+
+
+@pytest.mark.parametrize("heads,softmax", [(1, False), (1, True), (2, True), (4, True), (4, False)])
+def test_fusedmm_grad_f32(spk, heads, softmax):
+    M, N, K = 600, 450, 16 * heads
+    rp, ci, vals, A, B, dY = _case(M, N, K, seed=10 + heads + 5 * softmax)
+    scale = 1.0 / np.sqrt(K // heads)
+    S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV)
+    tA = torch.from_numpy(A).to(DEV).requires_grad_()
+    tB = torch.from_numpy(B).to(DEV).requires_grad_()
+    Y = spk.autograd.fusedmm(S, tA, tB, S.vals, heads=heads, scale=scale, softmax=softmax)
+    Yr, _, _ = oracle.fusedmm(rp, ci, A, B, vals, heads=heads, scale=scale, softmax=softmax)
+    Ya, _, _ = oracle.fusedmm(rp, ci, A, B, vals, heads=heads, scale=scale, softmax=softmax, absmode=True)
+    assert comp_err(Y.detach().cpu().numpy(), Yr, Ya) <= TOL
+    Y.backward(torch.from_numpy(dY).to(DEV))
+    dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, heads=heads, scale=scale, softmax=softmax)
+    assert _normwise(tA.grad.cpu().numpy(), dA) <= GRAD_TOL
+    assert _normwise(tB.grad.cpu().numpy(), dB) <= GRAD_TOL
+    empty = np.flatnonzero(np.diff(rp) == 0)
+    assert np.all(tA.grad.cpu().numpy()[empty] == 0.0)
+
+
+@pytest.mark.parametrize("softmax", [False, True])
+def test_fusedmm_grad_bf16_shared_operand(spk, softmax):
+    """A = B = H in BF16 (a square pattern): dH = dA + dB, each written in BF16."""
+    M, K, heads = 500, 32, 2
+    rp, ci, vals, H, _, dY = _case(M, M, K, seed=21 + softmax)
+    S = spk.CSR(rp, ci, (M, M), torch.from_numpy(vals), device=DEV)
+    tH = spk.cast(torch.from_numpy(H).to(DEV), torch.bfloat16).requires_grad_()
+    Hq = tH.detach().view(torch.int16).cpu().numpy().view(np.uint16)
+    Y = spk.autograd.fusedmm(S, tH, tH, S.vals, heads=heads, scale=0.25, softmax=softmax)
+    Y.backward(torch.from_numpy(dY).to(DEV))
+    dA, dB = oracle.fusedmm_grad(rp, ci, Hq, Hq, dY, vals, heads=heads, scale=0.25, softmax=softmax, fmt="bf16")
+    assert tH.grad.dtype == torch.bfloat16
+    assert _normwise(tH.grad.float().cpu().numpy(), dA + dB) <= 2 * GRAD_TOL_16
+
+
+def test_fusedmm_grad_matches_unfused_composition(spk):
+    """Without softmax, FusedMM is SpMM(S_e, B) with e = scale * SDDMM(S, A, B):
+    the fused layer's gradients equal those of the composed primitives."""
+    M, N, K = 400, 380, 32
+    rp, ci, vals, A, B, dY = _case(M, N, K, seed=31)
+    S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV)
+    a1 = torch.from_numpy(A).to(DEV).requires_grad_(); b1 = torch.from_numpy(B).to(DEV).requires_grad_()
+    spk.autograd.fusedmm(S, a1, b1, S.vals, scale=0.5).backward(torch.from_numpy(dY).to(DEV))
+    a2 = torch.from_numpy(A).to(DEV).requires_grad_(); b2 = torch.from_numpy(B).to(DEV).requires_grad_()
+    e = spk.autograd.sddmm(S, a2, b2, S.vals * 0.5)
+    spk.autograd.spmm(S, b2, e).backward(torch.from_numpy(dY).to(DEV))
+    for x, y in ((a1.grad, a2.grad), (b1.grad, b2.grad)):
+        assert _normwise(x.cpu().numpy(), y.double().cpu().numpy()) <= GRAD_TOL
