@@ -203,23 +203,27 @@ spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int32_t softma
 
 /* Steps of the FusedMM backward that are not SDDMM / SpMM calls.  Arrays
  * over entries are heads x nnz FP32 (head-major); lse and rowdot are M x heads
- * FP32; dY and Y are M x K FP32 row-major with row strides lddy, ldy.  For
- * entry e = (i, j) and head h (columns h*K/heads .. (h+1)*K/heads - 1):
+ * FP32; dY and Y are M x K FP32 row-major with row strides lddy, ldy; vals is
+ * the FusedMM's nnz sparse values (NULL = ones).  For entry e = (i, j) and
+ * head h (columns h*K/heads .. (h+1)*K/heads - 1):
  *   spk_fused_weights:    w = scores, or exp(scores - lse[i]) with softmax
  *   spk_fused_rowdot:     rowdot[i, h] = <dY_i, Y_i> over head h's columns,
  *                         which equals sum_j w_ij <dY_i, B_j> (the softmax
  *                         backward's row term; Y is the FusedMM output)
- *   spk_fused_score_grad: de = scale * dw, or scale * w * (dw - rowdot[i])
- *                         with softmax, where dw = <dY_i, B_j> per head
- * spk_fused_weights and spk_fused_score_grad need the balanced schedule
- * (its COO rows); none allocates.  The gradient w.r.t. the score before
- * scaling by the sparse value is de * s_e. */
+ *   spk_fused_score_grad: c = scale * s_e * dw, or
+ *                         scale * s_e * w * (dw - rowdot[i]) with softmax,
+ *                         where dw = <dY_i, B_j> per head: the gradient
+ *                         w.r.t. the unscaled dot <A_i, B_j>, so that
+ *                         dA = SpMM(c, B) and dB = SpMM^T(c, A) + SpMM^T(w, dY)
+ *                         per head, each with one value array
+ * heads is at most 65535.  spk_fused_weights and spk_fused_score_grad need
+ * the balanced schedule (its COO rows); none allocates. */
 spk_status spk_fused_weights(spk_csr S, int32_t heads, int32_t softmax, const float* scores, const float* lse,
                              float* w, void* stream);
 spk_status spk_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* dY, int64_t lddy, const float* Y,
                             int64_t ldy, float* rowdot, void* stream);
-spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* w,
-                                const float* dw, const float* rowdot, float* de, void* stream);
+spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* vals,
+                                const float* w, const float* dw, const float* rowdot, float* c, void* stream);
 
 /* ----------------------------------------------------- transpose plan -- */
 /* The CSC of S by a stable device radix sort on the column index: colptr[N+1],

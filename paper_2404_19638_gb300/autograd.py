@@ -126,9 +126,11 @@ class FusedMMFunction(torch.autograd.Function):
     Backward (chain rule, per head; dw_ij = <dY_i, B_j>):
       g = dw, or w * (dw - rowdot_i) with softmax, rowdot_i = sum_j w_ij dw_ij
           = <dY_i, Y_i> (read from the saved output)
-      c = scale * g;  dA = (S.c) B;  dB = (S.c)^T A + W^T dY
+      c = scale * s * g;  dA = C B;  dB = C^T A + W^T dY  (C, W: S's pattern
+      holding c, w)
     Steps: one SDDMM per head for dw, the row term and score gradient
-    kernels, then SpMM / SpMM^T per head accumulating in FP32.  The sparse
+    kernels (c folds in the sparse values, so every SpMM takes one value
+    array), then SpMM / SpMM^T per head accumulating in FP32.  The sparse
     values are not differentiated.
     """
 
@@ -155,20 +157,20 @@ class FusedMMFunction(torch.autograd.Function):
             c0 = h * Kh
             ops.sddmm(S, dY[:, c0:c0 + Kh], B[:, c0:c0 + Kh], out=dw[h], use_default_vals=False)
         R = ops.fused_rowdot(dY, Y, heads) if softmax else None
-        c = ops.fused_score_grad(S, w, dw, R, heads, softmax, scale)
+        c = ops.fused_score_grad(S, w, dw, R, heads, softmax, scale, v)
         dA = dB = None
         if ctx.needs_input_grad[2]:
             dA = torch.empty((S.M, K), dtype=torch.float32, device=S.device)
             for h in range(heads):
                 c0 = h * Kh
-                ops.spmm(S, B[:, c0:c0 + Kh], v, c[h], out=dA[:, c0:c0 + Kh], use_default_vals=False)
+                ops.spmm(S, B[:, c0:c0 + Kh], c[h], out=dA[:, c0:c0 + Kh], use_default_vals=False)
             if A.dtype != torch.float32:
                 dA = ops.cast(dA, A.dtype)
         if ctx.needs_input_grad[3]:
             dB = torch.empty((S.N, K), dtype=torch.float32, device=S.device)
             for h in range(heads):
                 c0 = h * Kh
-                ops.spmm_t(S, A[:, c0:c0 + Kh], v, c[h], out=dB[:, c0:c0 + Kh], use_default_vals=False)
+                ops.spmm_t(S, A[:, c0:c0 + Kh], c[h], out=dB[:, c0:c0 + Kh], use_default_vals=False)
                 ops.spmm_t(S, dY[:, c0:c0 + Kh], w[h], out=dB[:, c0:c0 + Kh], accumulate=True,
                            use_default_vals=False)
             if B.dtype != torch.float32:

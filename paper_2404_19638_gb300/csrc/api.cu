@@ -491,7 +491,8 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
 extern "C" spk_status spk_fused_weights(spk_csr S, int32_t heads, int32_t softmax, const float* scores,
                                         const float* lse, float* w, void* stream)
 {
-    REQUIRE(S && heads >= 1 && (softmax == 0 || softmax == 1), SPK_ERR_ARG, "spk_fused_weights: bad argument");
+    REQUIRE(S && heads >= 1 && heads <= 65535 && (softmax == 0 || softmax == 1), SPK_ERR_ARG,
+            "spk_fused_weights: bad argument");
     REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_fused_weights: needs spk_schedule_build first");
     REQUIRE(S->nnz == 0 || (scores && w && (!softmax || lse)), SPK_ERR_ARG, "spk_fused_weights: NULL array");
     cudaError_t e = launch_fused_weights(S->rowidx, S->nnz, heads, softmax, scores, lse, w, (cudaStream_t)stream);
@@ -511,14 +512,16 @@ extern "C" spk_status spk_fused_rowdot(int64_t M, int32_t K, int32_t heads, cons
     return SPK_OK;
 }
 
-extern "C" spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* w,
-                                           const float* dw, const float* rowdot, float* de, void* stream)
+extern "C" spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* vals,
+                                           const float* w, const float* dw, const float* rowdot, float* c,
+                                           void* stream)
 {
-    REQUIRE(S && heads >= 1 && (softmax == 0 || softmax == 1), SPK_ERR_ARG, "spk_fused_score_grad: bad argument");
+    REQUIRE(S && heads >= 1 && heads <= 65535 && (softmax == 0 || softmax == 1), SPK_ERR_ARG,
+            "spk_fused_score_grad: bad argument");
     REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_fused_score_grad: needs spk_schedule_build first");
-    REQUIRE(S->nnz == 0 || (dw && de && (!softmax || (w && rowdot))), SPK_ERR_ARG,
+    REQUIRE(S->nnz == 0 || (dw && c && (!softmax || (w && rowdot))), SPK_ERR_ARG,
             "spk_fused_score_grad: NULL array");
-    cudaError_t e = launch_fused_score_grad(S->rowidx, S->nnz, heads, softmax, scale, w, dw, rowdot, de,
+    cudaError_t e = launch_fused_score_grad(S->rowidx, S->nnz, heads, softmax, scale, vals, w, dw, rowdot, c,
                                             (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "spk_fused_score_grad");
     return SPK_OK;

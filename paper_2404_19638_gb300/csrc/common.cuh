@@ -408,7 +408,8 @@ cudaError_t launch_fused_weights(const int32_t* rowidx, int64_t nnz, int heads, 
 cudaError_t launch_fused_rowdot(int64_t M, int K, int heads, const float* dY, int64_t lddy, const float* Y,
                                 int64_t ldy, float* rowdot, cudaStream_t s);
 cudaError_t launch_fused_score_grad(const int32_t* rowidx, int64_t nnz, int heads, int softmax, float scale,
-                                    const float* w, const float* dw, const float* rowdot, float* de, cudaStream_t s);
+                                    const float* vals, const float* w, const float* dw, const float* rowdot,
+                                    float* c, cudaStream_t s);
 int fused_shape_index(int G, int NV, int U);   // -1 if not compiled
 cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const float* vals2, int64_t nnz, float* out,
                                 cudaStream_t s);

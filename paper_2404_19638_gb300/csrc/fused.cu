@@ -870,87 +870,155 @@ static cudaError_t launch_fused_t(const Launch& L, const FusedArgs& a, cudaStrea
 }
 
 // ----------------------------------------------------------------------------
-// Elementwise steps of the FusedMM backward, per head h and stored entry e of
-// row i (COO row from the schedule):
+// Elementwise steps of the FusedMM backward, per head h (grid row) and stored
+// entry e of row i (COO row from the schedule):
 //   weights:    w = e_h, or exp(e_h - lse[i, h]) with softmax
-//   score grad: de = scale * dw, or scale * w * (dw - rowdot[i, h]) with softmax
+//   score grad: c = scale * s_e * dw, or scale * s_e * w * (dw - rowdot[i, h])
+// Each thread takes kElemIlp entries a block-width apart (coalesced, several
+// loads in flight); the grid's x extent is a multiple of the SM count.
 // ----------------------------------------------------------------------------
-__global__ void k_fused_weights(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t heads, int32_t softmax,
-                                const float* __restrict__ scores, const float* __restrict__ lse, float* __restrict__ w)
+constexpr int kElemThreads = 256;
+constexpr int kElemIlp = 4;
+
+static unsigned elem_blocks(int64_t nnz)
 {
-    const int64_t n = nnz * heads;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t h = q / nnz, e = q - h * nnz;
-        const float sc = scores[q];
-        w[q] = softmax ? expf(sc - __ldg(lse + (int64_t)__ldg(rowidx + e) * heads + h)) : sc;
+    const int64_t per = (int64_t)kElemThreads * kElemIlp;
+    int64_t b = (nnz + per - 1) / per;
+    const int64_t cap = 152 * 8;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+__global__ void __launch_bounds__(kElemThreads) k_fused_weights(const int32_t* __restrict__ rowidx, int64_t nnz,
+                                                                int32_t heads, const float* __restrict__ scores,
+                                                                const float* __restrict__ lse, float* __restrict__ w)
+{
+    const int h = blockIdx.y;
+    const float* sc = scores + (int64_t)h * nnz;
+    float* wo = w + (int64_t)h * nnz;
+    const int64_t stride = (int64_t)gridDim.x * kElemThreads * kElemIlp;
+    for (int64_t base = (int64_t)blockIdx.x * kElemThreads * kElemIlp + threadIdx.x; base < nnz; base += stride) {
+        float x[kElemIlp];
+        int r[kElemIlp];
+#pragma unroll
+        for (int u = 0; u < kElemIlp; ++u) {
+            const int64_t e = base + (int64_t)u * kElemThreads;
+            x[u] = e < nnz ? __ldg(sc + e) : 0.f;
+            r[u] = e < nnz ? __ldg(rowidx + e) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kElemIlp; ++u) {
+            const int64_t e = base + (int64_t)u * kElemThreads;
+            if (e < nnz) wo[e] = expf(x[u] - __ldg(lse + (int64_t)r[u] * heads + h));
+        }
     }
 }
 
-__global__ void k_fused_score_grad(const int32_t* __restrict__ rowidx, int64_t nnz, int32_t heads, int32_t softmax,
-                                   float scale, const float* __restrict__ w, const float* __restrict__ dw,
-                                   const float* __restrict__ rowdot, float* __restrict__ de)
+template <bool SOFTMAX>
+__global__ void __launch_bounds__(kElemThreads) k_fused_score_grad(const int32_t* __restrict__ rowidx, int64_t nnz,
+                                                                   int32_t heads, float scale,
+                                                                   const float* __restrict__ vals,
+                                                                   const float* __restrict__ w,
+                                                                   const float* __restrict__ dw,
+                                                                   const float* __restrict__ rowdot,
+                                                                   float* __restrict__ c)
 {
-    const int64_t n = nnz * heads;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t h = q / nnz, e = q - h * nnz;
-        float g = dw[q];
-        if (softmax) g = w[q] * (g - __ldg(rowdot + (int64_t)__ldg(rowidx + e) * heads + h));
-        de[q] = scale * g;
+    const int h = blockIdx.y;
+    const int64_t off = (int64_t)h * nnz;
+    const int64_t stride = (int64_t)gridDim.x * kElemThreads * kElemIlp;
+    for (int64_t base = (int64_t)blockIdx.x * kElemThreads * kElemIlp + threadIdx.x; base < nnz; base += stride) {
+        float g[kElemIlp], ww[kElemIlp], s[kElemIlp];
+        int r[kElemIlp];
+#pragma unroll
+        for (int u = 0; u < kElemIlp; ++u) {
+            const int64_t e = base + (int64_t)u * kElemThreads;
+            const bool in = e < nnz;
+            g[u] = in ? __ldg(dw + off + e) : 0.f;
+            s[u] = (in && vals) ? __ldg(vals + e) : 1.f;
+            if constexpr (SOFTMAX) {
+                ww[u] = in ? __ldg(w + off + e) : 0.f;
+                r[u] = in ? __ldg(rowidx + e) : 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kElemIlp; ++u) {
+            const int64_t e = base + (int64_t)u * kElemThreads;
+            if (e >= nnz) continue;
+            float v = g[u];
+            if constexpr (SOFTMAX) v = ww[u] * (v - __ldg(rowdot + (int64_t)r[u] * heads + h));
+            c[off + e] = (scale * s[u]) * v;
+        }
     }
 }
 
 // rowdot[i, h] = <dY[i, head h], Y[i, head h]>: with Y[i, h] = sum_j w_ij B[j, h]
 // this equals sum_j w_ij <dY_i, B_j> = sum_j w_ij dw_ij, the softmax
 // backward's row term, read from two dense rows instead of a sparse row
-// (balanced whatever the degree).  One warp per row.
-__global__ void k_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* __restrict__ dY, int64_t lddy,
-                               const float* __restrict__ Y, int64_t ldy, float* __restrict__ rowdot)
+// (balanced whatever the degree).  One thread per (row, head); 16-byte loads
+// when the head's columns and both row strides allow them.
+template <bool V4>
+__global__ void __launch_bounds__(kElemThreads) k_fused_rowdot(int64_t M, int32_t Kh, int32_t heads,
+                                                               const float* __restrict__ dY, int64_t lddy,
+                                                               const float* __restrict__ Y, int64_t ldy,
+                                                               float* __restrict__ rowdot)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int Kh = K / heads;
-    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < M; i += warps) {
-        const float* g = dY + i * lddy;
-        const float* y = Y + i * ldy;
-        for (int h = 0; h < heads; ++h) {
-            float acc = 0.f;
-            for (int c = h * Kh + lane; c < (h + 1) * Kh; c += 32) acc = fmaf(__ldg(g + c), __ldg(y + c), acc);
-#pragma unroll
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) rowdot[i * heads + h] = acc;
+    const int64_t n = M * heads;
+    for (int64_t q = (int64_t)blockIdx.x * kElemThreads + threadIdx.x; q < n; q += (int64_t)gridDim.x * kElemThreads) {
+        const int64_t i = q / heads;
+        const int h = (int)(q - i * heads);
+        const float* g = dY + i * lddy + (int64_t)h * Kh;
+        const float* y = Y + i * ldy + (int64_t)h * Kh;
+        float a0 = 0.f, a1 = 0.f;
+        if constexpr (V4) {
+            for (int c = 0; c < Kh; c += 4) {
+                const float4 gv = __ldg(reinterpret_cast<const float4*>(g + c));
+                const float4 yv = __ldg(reinterpret_cast<const float4*>(y + c));
+                a0 = fmaf(gv.x, yv.x, a0); a1 = fmaf(gv.y, yv.y, a1);
+                a0 = fmaf(gv.z, yv.z, a0); a1 = fmaf(gv.w, yv.w, a1);
+            }
+        } else {
+            for (int c = 0; c < Kh; ++c) a0 = fmaf(__ldg(g + c), __ldg(y + c), a0);
         }
+        rowdot[q] = a0 + a1;
     }
 }
 
 cudaError_t launch_fused_rowdot(int64_t M, int K, int heads, const float* dY, int64_t lddy, const float* Y,
                                 int64_t ldy, float* rowdot, cudaStream_t s)
 {
-    if (M <= 0) return cudaSuccess;
-    int64_t blocks = (M + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_fused_rowdot<<<(unsigned)blocks, 256, 0, s>>>(M, K, heads, dY, lddy, Y, ldy, rowdot);
+    const int64_t n = M * heads;
+    if (n <= 0) return cudaSuccess;
+    const int Kh = K / heads;
+    int64_t blocks = (n + kElemThreads - 1) / kElemThreads;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    const bool v4 = Kh % 4 == 0 && (reinterpret_cast<uintptr_t>(dY) & 15u) == 0 &&
+                    (reinterpret_cast<uintptr_t>(Y) & 15u) == 0 && (M <= 1 || (lddy % 4 == 0 && ldy % 4 == 0));
+    if (v4) k_fused_rowdot<true><<<(unsigned)blocks, kElemThreads, 0, s>>>(M, Kh, heads, dY, lddy, Y, ldy, rowdot);
+    else k_fused_rowdot<false><<<(unsigned)blocks, kElemThreads, 0, s>>>(M, Kh, heads, dY, lddy, Y, ldy, rowdot);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused_weights(const int32_t* rowidx, int64_t nnz, int heads, int softmax, const float* scores,
                                  const float* lse, float* w, cudaStream_t s)
 {
-    const int64_t n = nnz * heads;
-    if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_fused_weights<<<(unsigned)blocks, 256, 0, s>>>(rowidx, nnz, heads, softmax, scores, lse, w);
+    if (nnz <= 0 || heads <= 0) return cudaSuccess;
+    if (!softmax)
+        return cudaMemcpyAsync(w, scores, (size_t)nnz * heads * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    k_fused_weights<<<dim3(elem_blocks(nnz), (unsigned)heads), kElemThreads, 0, s>>>(rowidx, nnz, heads, scores,
+                                                                                     lse, w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused_score_grad(const int32_t* rowidx, int64_t nnz, int heads, int softmax, float scale,
-                                    const float* w, const float* dw, const float* rowdot, float* de, cudaStream_t s)
+                                    const float* vals, const float* w, const float* dw, const float* rowdot,
+                                    float* c, cudaStream_t s)
 {
-    const int64_t n = nnz * heads;
-    if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_fused_score_grad<<<(unsigned)blocks, 256, 0, s>>>(rowidx, nnz, heads, softmax, scale, w, dw, rowdot, de);
+    if (nnz <= 0 || heads <= 0) return cudaSuccess;
+    const dim3 grid(elem_blocks(nnz), (unsigned)heads);
+    if (softmax)
+        k_fused_score_grad<true><<<grid, kElemThreads, 0, s>>>(rowidx, nnz, heads, scale, vals, w, dw, rowdot, c);
+    else
+        k_fused_score_grad<false><<<grid, kElemThreads, 0, s>>>(rowidx, nnz, heads, scale, vals, w, dw, rowdot, c);
     return cudaGetLastError();
 }
 

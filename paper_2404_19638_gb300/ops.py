@@ -188,16 +188,18 @@ def fused_rowdot(dY: torch.Tensor, Y: torch.Tensor, heads: int) -> torch.Tensor:
 
 
 def fused_score_grad(S: CSR, w: torch.Tensor, dw: torch.Tensor, rowdot, heads: int, softmax: bool,
-                     scale: float) -> torch.Tensor:
-    """Gradient w.r.t. the scaled dot products: scale * dw, or
-    scale * w * (dw - rowdot[row]) with softmax.  heads x nnz FP32."""
+                     scale: float, vals=None) -> torch.Tensor:
+    """Gradient w.r.t. the unscaled dot products <A_i, B_j>: scale * s * dw, or
+    scale * s * w * (dw - rowdot[row]) with softmax (s = vals, None = ones).
+    heads x nnz FP32."""
     for t, name in ((w, "w"), (dw, "dw")):
         if t.shape != (heads, S.nnz) or t.dtype != torch.float32:
             raise ValueError(f"{name} must be heads x nnz float32")
     if softmax and (rowdot is None or rowdot.shape != (S.M, heads)):
         raise ValueError("softmax score gradient needs rowdot (M x heads float32)")
+    vals = _vals(vals, S, "vals")
     de = torch.empty_like(dw)
-    check(lib().spk_fused_score_grad(S.handle, int(heads), int(bool(softmax)), float(scale),
+    check(lib().spk_fused_score_grad(S.handle, int(heads), int(bool(softmax)), float(scale), _ptr(vals),
                                      w.contiguous().data_ptr(), dw.contiguous().data_ptr(),
                                      _ptr(rowdot.contiguous() if softmax else None), de.data_ptr(),
                                      _stream(S.device)), "spk_fused_score_grad")

@@ -128,7 +128,8 @@ def test_fused_backward_steps_reject_bad_arguments(L):
     assert L.spk_fused_weights(h, 2, 1, 4096, 8192, 12288, None) == 9        # no schedule: needs the COO rows
     assert L.spk_fused_weights(h, 0, 0, 4096, None, 12288, None) == 1        # heads < 1
     assert L.spk_fused_weights(h, 1, 2, 4096, None, 12288, None) == 1        # softmax flag not 0/1
-    assert L.spk_fused_score_grad(h, 2, 1, 1.0, 4096, 8192, 12288, 16384, None) == 9
+    assert L.spk_fused_score_grad(h, 2, 1, 1.0, None, 4096, 8192, 12288, 16384, None) == 9
+    assert L.spk_fused_score_grad(h, 70000, 0, 1.0, None, None, 8192, None, 16384, None) == 1   # heads > 65535
     assert L.spk_fused_rowdot(10, 12, 5, 4096, 12, 8192, 12, 12288, None) == 2   # K not a multiple of heads
     assert L.spk_fused_rowdot(10, 12, 3, 4096, 8, 8192, 12, 12288, None) == 2    # row stride below K
     assert L.spk_fused_rowdot(10, 12, 3, None, 12, 8192, 12, 12288, None) == 1

@@ -66,7 +66,8 @@ def test_weights_kernel(spk):
 
 def test_rowdot_kernel(spk):
     g = np.random.default_rng(2)
-    for (M, K, heads) in [(1, 4, 1), (333, 96, 3), (1000, 64, 4), (77, 40, 5)]:
+    # 16-byte path (head width a multiple of 4) and scalar path (3, 5, 9 columns)
+    for (M, K, heads) in [(1, 4, 1), (333, 96, 3), (1000, 64, 4), (77, 40, 5), (50, 9, 3), (64, 25, 5), (5, 9, 1)]:
         dY = g.standard_normal((M, K)).astype(np.float32)
         Y = g.standard_normal((M, K)).astype(np.float32)
         R = spk.ops.fused_rowdot(torch.from_numpy(dY).to(DEV), torch.from_numpy(Y).to(DEV), heads).cpu().numpy()
@@ -81,6 +82,10 @@ def test_rowdot_kernel(spk):
     R = spk.ops.fused_rowdot(W[:, 16:48], Y, 2).cpu().numpy()
     p = W[:, 16:48].double().cpu().numpy() * Y.double().cpu().numpy()
     assert comp_err(R, p.reshape(50, 2, 16).sum(2), np.abs(p).reshape(50, 2, 16).sum(2)) <= TOL
+    # a 4-byte-aligned column offset falls back to scalar loads
+    R = spk.ops.fused_rowdot(W[:, 1:13], Y[:, :12], 3).cpu().numpy()
+    p = W[:, 1:13].double().cpu().numpy() * Y[:, :12].double().cpu().numpy()
+    assert comp_err(R, p.reshape(50, 3, 4).sum(2), np.abs(p).reshape(50, 3, 4).sum(2)) <= TOL
     # M = 0 is a no-op
     E = torch.empty((0, 8), device=DEV)
     assert spk.ops.fused_rowdot(E, E, 2).shape == (0, 2)
@@ -95,17 +100,21 @@ def test_score_grad_kernel(spk, softmax):
     w = g.uniform(0, 1, (heads, nnz)).astype(np.float32)
     dw = g.standard_normal((heads, nnz)).astype(np.float32)
     R = g.standard_normal((400, heads)).astype(np.float32)
-    de = spk.ops.fused_score_grad(S, torch.from_numpy(w).to(DEV), torch.from_numpy(dw).to(DEV),
-                                  torch.from_numpy(R).to(DEV), heads, softmax, 0.3).cpu().numpy()
+    s = g.uniform(-2, 2, nnz).astype(np.float32)
     rows = row_of(rp)
     w64, dw64, R64 = w.astype(np.float64), dw.astype(np.float64), R.astype(np.float64)[rows].T
-    if softmax:
-        ref = 0.3 * w64 * (dw64 - R64)
-        den = 0.3 * w64 * (np.abs(dw64) + np.abs(R64))
-    else:
-        ref = 0.3 * dw64
-        den = np.abs(ref)
-    assert comp_err(de, ref, den) <= TOL
+    for vals in (None, s):
+        de = spk.ops.fused_score_grad(S, torch.from_numpy(w).to(DEV), torch.from_numpy(dw).to(DEV),
+                                      torch.from_numpy(R).to(DEV), heads, softmax, 0.3,
+                                      None if vals is None else torch.from_numpy(vals).to(DEV)).cpu().numpy()
+        s64 = 1.0 if vals is None else vals.astype(np.float64)
+        if softmax:
+            ref = 0.3 * s64 * w64 * (dw64 - R64)
+            den = np.abs(0.3 * s64) * w64 * (np.abs(dw64) + np.abs(R64))
+        else:
+            ref = 0.3 * s64 * dw64
+            den = np.abs(ref)
+        assert comp_err(de, ref, den) <= TOL
 
 
 @pytest.mark.parametrize("heads,softmax", [(1, False), (1, True), (2, True), (4, True), (4, False)])
