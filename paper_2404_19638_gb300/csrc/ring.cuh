@@ -482,11 +482,8 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                     j[4 * c + 3] = __shfl_sync(g.mask, tc.w, src0 + c, G);
                 }
                 const int eb = tb0 + b * U;
-                const bool full = (eb >= e0) && (eb + U <= e1);
                 Vec* sl = wring + (b & 1) * U * NV * 32 + lane;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (!full && (eb + u < e0 || eb + u >= e1)) continue;
+                auto copy_row = [&](int u) {
                     const char* brow = Bb + (size_t)(unsigned)j[u] * ldb_bytes;
 #pragma unroll
                     for (int t2 = 0; t2 < NV; ++t2)
@@ -494,6 +491,23 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                             if constexpr (VB == 16) cpa16(sl + (u * NV + t2) * 32, brow + t2 * G * 16);
                             else cpa8(sl + (u * NV + t2) * 32, brow + t2 * G * 8);
                         }
+                };
+                if constexpr (DT == DT_F32 && U >= 8) {
+                    if (eb >= e0 && eb + U <= e1) {     // whole batch inside the span: no per-entry guard
+#pragma unroll
+                        for (int u = 0; u < U; ++u) copy_row(u);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (eb + u >= e0 && eb + u < e1) copy_row(u);
+                    }
+                } else {                                // 16-bit rows, short batches: one guarded loop
+                    const bool full = (eb >= e0) && (eb + U <= e1);
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!full && (eb + u < e0 || eb + u >= e1)) continue;
+                        copy_row(u);
+                    }
                 }
             }
             cp_async_commit();
@@ -531,6 +545,34 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                         unpack_vec<DT, VECN>(sl[(u * NV + t) * 32], bf);
                         axpy_pairs<VECN>(acc[t], sc[u], bf);
                     }
+            } else if constexpr (DT == DT_F32 && U >= 8) {
+                // a row ends inside the batch, or the batch straddles the
+                // span's ends: one copy of the row-change code, entries read
+                // back from the staged tiles by a runtime index (measured
+                // 3 % faster for FP32 rows in batches of 8; 7 % slower for
+                // 16-bit rows and 14 % slower for FP32 batches of 4)
+                const int u0 = max(e0 - eb, 0), u1 = min(e1 - eb, U);
+#pragma unroll 1
+                for (int u = u0; u < u1; ++u) {
+                    const int r = trow[o + u];
+                    if (r != cur) {
+                        flush(cur);
+                        for (int rr = cur + 1; rr < r; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
+                        cur = r;
+#pragma unroll
+                        for (int t = 0; t < NV; ++t)
+#pragma unroll
+                            for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
+                    }
+                    const float sv = vals ? tval[o + u] : 1.f;
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) {
+                        if (!vin[t]) continue;
+                        float bf[VECN];
+                        unpack_vec<DT, VECN>(sl[(u * NV + t) * 32], bf);
+                        axpy_pairs<VECN>(acc[t], sv, bf);
+                    }
+                }
             } else {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
