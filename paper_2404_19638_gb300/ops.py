@@ -160,17 +160,22 @@ def fusedmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, *, heads: int =
     return out, scores, lse
 
 
+def _f32(t, shape, name, device):
+    """A float32 tensor of the given shape on the pattern's device, or raise
+    (no host pointer ever reaches a kernel)."""
+    if t is None or t.dtype != torch.float32 or tuple(t.shape) != tuple(shape) or t.device != device:
+        raise ValueError(f"{name} must be a float32 tensor of shape {tuple(shape)} on {device}")
+    return t.contiguous()
+
+
 def fused_weights(S: CSR, scores: torch.Tensor, lse, heads: int, softmax: bool) -> torch.Tensor:
     """Per-entry weights of a FusedMM forward: the scores, or exp(score - lse[row])
     with softmax.  heads x nnz FP32."""
-    if scores.shape != (heads, S.nnz) or scores.dtype != torch.float32:
-        raise ValueError("scores must be heads x nnz float32")
-    if softmax and (lse is None or lse.shape != (S.M, heads) or lse.dtype != torch.float32):
-        raise ValueError("softmax weights need lse (M x heads float32)")
+    scores = _f32(scores, (heads, S.nnz), "scores", S.device)
+    lse = _f32(lse, (S.M, heads), "lse", S.device) if softmax else None
     w = torch.empty_like(scores)
-    check(lib().spk_fused_weights(S.handle, int(heads), int(bool(softmax)), scores.contiguous().data_ptr(),
-                                  _ptr(lse.contiguous() if softmax else None), w.data_ptr(), _stream(S.device)),
-          "spk_fused_weights")
+    check(lib().spk_fused_weights(S.handle, int(heads), int(bool(softmax)), scores.data_ptr(), _ptr(lse),
+                                  w.data_ptr(), _stream(S.device)), "spk_fused_weights")
     return w
 
 
@@ -178,6 +183,8 @@ def fused_rowdot(dY: torch.Tensor, Y: torch.Tensor, heads: int) -> torch.Tensor:
     """rowdot[i, h] = <dY_i, Y_i> over head h's columns.  M x heads FP32."""
     if dY.dtype != torch.float32 or Y.dtype != torch.float32 or dY.shape != Y.shape or dY.dim() != 2:
         raise ValueError("dY and Y must be M x K float32 of one shape")
+    if not dY.is_cuda or Y.device != dY.device:
+        raise ValueError("dY and Y must be CUDA tensors on one device")
     _, lddy = _dense(dY, "dY", dY.device)
     _, ldy = _dense(Y, "Y", dY.device)
     M, K = Y.shape
@@ -192,17 +199,14 @@ def fused_score_grad(S: CSR, w: torch.Tensor, dw: torch.Tensor, rowdot, heads: i
     """Gradient w.r.t. the unscaled dot products <A_i, B_j>: scale * s * dw, or
     scale * s * w * (dw - rowdot[row]) with softmax (s = vals, None = ones).
     heads x nnz FP32."""
-    for t, name in ((w, "w"), (dw, "dw")):
-        if t.shape != (heads, S.nnz) or t.dtype != torch.float32:
-            raise ValueError(f"{name} must be heads x nnz float32")
-    if softmax and (rowdot is None or rowdot.shape != (S.M, heads)):
-        raise ValueError("softmax score gradient needs rowdot (M x heads float32)")
+    dw = _f32(dw, (heads, S.nnz), "dw", S.device)
+    w = _f32(w, (heads, S.nnz), "w", S.device) if softmax else None
+    rowdot = _f32(rowdot, (S.M, heads), "rowdot", S.device) if softmax else None
     vals = _vals(vals, S, "vals")
     de = torch.empty_like(dw)
-    check(lib().spk_fused_score_grad(S.handle, int(heads), int(bool(softmax)), float(scale), _ptr(vals),
-                                     w.contiguous().data_ptr(), dw.contiguous().data_ptr(),
-                                     _ptr(rowdot.contiguous() if softmax else None), de.data_ptr(),
-                                     _stream(S.device)), "spk_fused_score_grad")
+    check(lib().spk_fused_score_grad(S.handle, int(heads), int(bool(softmax)), float(scale), _ptr(vals), _ptr(w),
+                                     dw.data_ptr(), _ptr(rowdot), de.data_ptr(), _stream(S.device)),
+          "spk_fused_score_grad")
     return de
 
 

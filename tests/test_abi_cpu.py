@@ -135,3 +135,16 @@ def test_fused_backward_steps_reject_bad_arguments(L):
     assert L.spk_fused_rowdot(10, 12, 3, None, 12, 8192, 12, 12288, None) == 1
     assert L.spk_fused_rowdot(0, 12, 3, None, 12, None, 12, None, None) == 0     # empty: nothing to do
     L.spk_csr_destroy(h)
+
+
+def test_python_wrappers_reject_host_tensors():
+    """Host tensors never reach a kernel: the wrappers raise first."""
+    import torch
+    from paper_2404_19638_gb300 import ops
+    X = torch.zeros((4, 8), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        ops.fused_rowdot(X, X, 2)
+    with pytest.raises(TypeError):
+        ops.cast(X, torch.bfloat16)
+    with pytest.raises(TypeError):
+        ops.quantize_e4m3_rows(X)
