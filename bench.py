@@ -547,8 +547,9 @@ def main(args):
         t = time_oracle_step(P, rows)
         line["cpu_baseline"] = {"value": 2.0 * 2.0 * nnz * K / t / 1e9, "unit": "GFLOP/s", "cores": 1,
                                 "kind": "oracle",
-                                "sample": f"every {stride}-th row ({nnz:,} of {P.nnz:,} nonzeros), SDDMM + SpMM "
-                                          f"in the FP64 oracle on one host core, {t:.1f} s"}
+                                "sample": (("all rows" if stride == 1 else f"every {stride}-th row")
+                                           + f" ({nnz:,} of {P.nnz:,} nonzeros), SDDMM + SpMM in the FP64 "
+                                           f"oracle on one host core, {t:.1f} s")}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
