@@ -501,3 +501,35 @@ def test_fusedmm_gradient_softmax_rows_sum_to_zero_in_scores():
     # scores in a row are equal, weights uniform, and a change of a_i shifts
     # every score of the row by the same amount: Y does not move
     np.testing.assert_allclose(dA, 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("heads,softmax", [(1, False), (2, True), (3, True)])
+def test_fusedmm_gradient_against_dense_autograd(heads, softmax):
+    """The oracle's FusedMM chain rule against reverse-mode differentiation of
+    a dense masked formulation (torch autograd, FP64), to rounding."""
+    import torch
+    M, N, K = 17, 13, 4 * heads
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=60 + heads)
+    g = np.random.default_rng(61)
+    dY = g.standard_normal((M, K))
+    scale = 0.7
+    dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, heads=heads, scale=scale, softmax=softmax)
+    S = torch.from_numpy(dense(rp, ci, vals.astype(np.float64), M, N))
+    mask = torch.from_numpy(dense(rp, ci, None, M, N) > 0)
+    tA = torch.from_numpy(A.astype(np.float64)).requires_grad_()
+    tB = torch.from_numpy(B.astype(np.float64)).requires_grad_()
+    D = K // heads
+    parts = []
+    for h in range(heads):
+        Ah, Bh = tA[:, h * D:(h + 1) * D], tB[:, h * D:(h + 1) * D]
+        E = scale * S * (Ah @ Bh.T)
+        if softmax:
+            W = torch.softmax(E.masked_fill(~mask, float("-inf")), dim=1)
+            W = torch.where(mask, W, torch.zeros_like(W))          # empty rows: no weights
+        else:
+            W = torch.where(mask, E, torch.zeros_like(E))
+        parts.append(W @ Bh)
+    Y = torch.cat(parts, dim=1)
+    gA, gB = torch.autograd.grad((torch.from_numpy(dY) * Y).sum(), (tA, tB))
+    np.testing.assert_allclose(dA, gA.numpy(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(dB, gB.numpy(), rtol=1e-10, atol=1e-12)
