@@ -217,8 +217,8 @@ spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int32_t softma
  *                         dA = SpMM(c, B) and dB = SpMM^T(c, A) + SpMM^T(w, dY)
  *                         per head, each with one value array
  * heads is at most 65535.  spk_fused_weights and spk_fused_score_grad need
- * the balanced schedule (its COO rows); none allocates.  w must not overlap
- * scores; c may be dw itself (each entry is read before it is written). */
+ * the balanced schedule (its COO rows); none allocates.  Outputs must not
+ * overlap inputs (w and scores; c and vals, w, dw, rowdot; rowdot and dY, Y). */
 spk_status spk_fused_weights(spk_csr S, int32_t heads, int32_t softmax, const float* scores, const float* lse,
                              float* w, void* stream);
 spk_status spk_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* dY, int64_t lddy, const float* Y,
