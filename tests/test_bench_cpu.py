@@ -31,3 +31,17 @@ def test_reference_arm_line():
 def test_warmup_floor():
     d = _run("--impl", "reference", "--workload", "tiny", "--steps", "1", "--warmup", "1")
     assert d["warmup"] >= 3
+
+
+def test_threaded_oracle_timing_covers_the_sample():
+    """The all-cores CPU baseline runs the unchanged oracle on interleaved row
+    shares; the shares partition the sample exactly."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    P, _ = bench.load_workload("tiny")
+    rows, nnz, stride = bench.oracle_sample_rows(P, 0, 20_000)
+    shares = [rows[t::3] for t in range(3)]
+    assert np.array_equal(np.sort(np.concatenate(shares)), rows)
+    assert bench.time_oracle_step_threads(P, rows, 3) > 0
+    assert bench.host_cores() >= 1
