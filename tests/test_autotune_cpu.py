@@ -39,3 +39,22 @@ def test_signature_separates_patterns():
     assert s1 != pattern_signature(rp1, 1000, 1001)
     empty = np.zeros(5, np.int32)
     assert pattern_signature(empty, 4, 4) != pattern_signature(np.arange(5, dtype=np.int32), 4, 4)
+
+
+def test_cache_round_trip_and_lookup(tmp_path):
+    """Entries persist through the JSON cache and are found again by the key of
+    a pattern with the same signature (host-only stand-in for a CSR)."""
+    import types
+    from paper_2404_19638_gb300.autotune import Autotuner
+    rp, _ = synth.er_exact_degree(500, 400, 6, seed=2)
+    S = types.SimpleNamespace(rowptr=torch.from_numpy(rp), M=500, N=400)
+    path = tmp_path / "tune.json"
+    t1 = Autotuner(cache_path=str(path))
+    assert t1.lookup(S, "spmm", torch.float32, 64) is None
+    key = t1.key(S, "spmm", torch.float32, 64)
+    t1._cache[key] = {"group_lanes": 16, "vecs_per_lane": 1, "unroll": 8, "chunk_work": 512}
+    t1._save()
+    t2 = Autotuner(cache_path=str(path))
+    assert t2.lookup(S, "spmm", torch.float32, 64) == t1._cache[key]
+    assert t2.lookup(S, "spmm", torch.bfloat16, 64) is None          # dtype is part of the key
+    assert t2.lookup(S, "sddmm", torch.float32, 64) is None          # so is the operation
