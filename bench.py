@@ -385,9 +385,24 @@ def aux_measurements(spk, S, P, A32, A, B, dt, elt, flush, stream, args):
             spk.autograd.fusedmm(S, Ag, Bg, S.vals, heads=4, softmax=True).backward(dY)
         out["fusedmm_softmax_4heads_fwd_bwd_ms"] = event_ms(fwd_bwd, stream, flush)
         del Ag, Bg, dY
+    if P.M == P.N:
+        # the attention-style graph layer Y = SpMM(S_e, H), e = SDDMM(S, H, H),
+        # differentiated: forward, then dH through SDDMM, SpMM and two SpMM^T
+        try:
+            Hg = A.detach().clone().requires_grad_()
+            dYl = torch.ones((P.M, P.K), dtype=torch.float32, device=dev)
+
+            def gnn_fwd_bwd():
+                Hg.grad = None
+                spk.autograd.gnn_layer(S, Hg).backward(dYl)
+            out["gnn_layer_fwd_bwd_ms"] = event_ms(gnn_fwd_bwd, stream, flush)
+            del Hg, dYl
+        except Exception as exc:                    # keep the line if this extra figure fails
+            out["gnn_layer_fwd_bwd_error"] = str(exc)[:200]
     out["note"] = ("measured after the timed step on the same pattern; builds by wall clock, kernels by CUDA "
                    "events with the L2 flushed; layer_separate = SDDMM then SpMM on its scores, fusedmm = the "
-                   "same layer in one kernel; fwd_bwd = that layer differentiated (forward, then dA and dB)")
+                   "same layer in one kernel; fwd_bwd = that layer differentiated (forward, then dA and dB); "
+                   "gnn_layer_fwd_bwd = the separate-kernel layer with H as both factors, forward then dH")
     return out
 
 
