@@ -61,3 +61,14 @@ def test_batch_workload_small():
         check_csr(p.rowptr, p.colidx, p.M, p.N)
         assert p.K in (16, 32, 64)
     assert ps[0].meta["kind"] == "er" and ps[-1].meta["kind"] == "rmat"
+
+
+def test_rmat20_pattern_matches_the_recorded_figures():
+    """The recorded rmat20 pattern (nnz after deduplication, empty rows, the
+    heaviest row) that the measurements and their GFLOP/s use."""
+    rp, ci = synth.rmat(20, 16, seed=0)
+    check_csr(rp, ci, 1 << 20, 1 << 20)
+    deg = np.diff(rp.astype(np.int64))
+    assert ci.size == 16_086_730
+    assert int(deg.max()) == 39_513
+    assert round(float(np.mean(deg == 0)), 2) == 0.48
