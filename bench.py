@@ -229,6 +229,9 @@ def reference_arm_batch(args):
     import oracle
     oracle.build()
     probs = synth.batch(seed=0)
+    for p in probs:                 # FP64 values for the oracle (exact from FP32), converted once, untimed
+        if p.vals is not None:
+            p.vals = p.vals.astype(np.float64)
     times, flops = [], []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -264,6 +267,8 @@ def reference_arm(args):
     P, desc = load_workload(args.workload)
     import oracle
     oracle.build()
+    if P.vals is not None:          # the oracle takes values in FP64 (exact from FP32): convert once, untimed
+        P.vals = P.vals.astype(np.float64)
     target = args.ref_nnz
     times, flops = [], []
     for s in range(args.warmup + args.steps):
@@ -585,6 +590,8 @@ def main(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        if P.vals is not None:      # FP64 values for the oracle (exact from FP32), converted once, untimed
+            P.vals = P.vals.astype(np.float64)
         rows, nnz, stride = oracle_sample_rows(P, 0, args.cpu_nnz)
         t = time_oracle_step(P, rows)
         cores = min(host_cores(), 64)               # each thread holds an nnz-long output while it runs
@@ -742,6 +749,9 @@ def main_batch(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        for *_, p in keep[::2]:        # FP64 values for the oracle (exact from FP32), converted once, untimed
+            if p.vals is not None:
+                p.vals = p.vals.astype(np.float64)
         t0 = time.perf_counter()
         fl = 0.0
         used = 0
