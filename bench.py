@@ -12,7 +12,7 @@ Prints one JSON line (rank 0).  With torchrun, every rank runs an independent
 replica on its own GPU (the step has no data exchange) and the line reports
 the aggregate over ranks, timed by the slowest rank.
 
---impl reference times the FP64 CPU oracle (the reference of this build) on a
+--impl reference times the FP64 CPU oracle (the reference implementation) on a
 bounded row sample of the same workload on the host cores.
 """
 from __future__ import annotations

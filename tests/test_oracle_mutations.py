@@ -43,7 +43,7 @@ MUTATIONS = [
     ("FusedMM gradient drops the scale", "__init__.py", "c = scale * g", "c = g"),
 ]
 
-_DRIVER = (
+_RUNNER = (
     "import sys; sys.path[:0] = [{copy!r}, {root!r}]\n"
     "import pytest\n"
     "sys.exit(pytest.main([{pins!r}, '-q', '-x', '-p', 'no:cacheprovider']))\n"
@@ -59,8 +59,8 @@ def _run_mutant(tmp, idx, name, fname, old, new):
     src = open(path).read()
     assert src.count(old) >= 1, f"{name}: anchor text not found in {fname}"
     open(path, "w").write(src.replace(old, new, 1))
-    driver = _DRIVER.format(copy=base, root=ROOT, pins=os.path.join(ROOT, "tests", "test_oracle_pins.py"))
-    r = subprocess.run([sys.executable, "-c", driver], capture_output=True, text=True, timeout=600, cwd=base)
+    runner = _RUNNER.format(copy=base, root=ROOT, pins=os.path.join(ROOT, "tests", "test_oracle_pins.py"))
+    r = subprocess.run([sys.executable, "-c", runner], capture_output=True, text=True, timeout=600, cwd=base)
     return name, r.returncode, r.stdout[-400:]
 
 
