@@ -107,34 +107,95 @@ def profiled_traffic(workload: str, dtype: str):
 # ----------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ----------------------------------------------------------------------------
+class _Nvml:
+    """Minimal ctypes access to NVML (read-only queries: clocks and the active
+    clock-event reasons); None where the library is absent."""
+    SM = 1                                   # NVML_CLOCK_SM
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index: int):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        m = ctypes.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, ctypes.byref(m))
+        self.max_mhz = float(m.value)
+
+    def sample(self):
+        c, r = self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.ct.byref(c)) != 0:
+            return None
+        self.reasons_fn(self.h, self.ct.byref(r))
+        return float(c.value), self.max_mhz, [n for b, n in self.REASONS.items() if r.value & b]
+
+
 class ClockSampler:
+    """SM clock and clock-event reasons sampled during the timed region: NVML
+    every millisecond where the library loads (a 20-step region of ~20 ms still
+    gets tens of samples), else nvidia-smi every 100 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_s: float = 0.001):
         self.gpu = gpu_index
+        self.period = period_s
         self.proc = None
-        self.lines = []                       # (host time of arrival, csv line)
+        self.nvml = None
+        self.stop = False
+        self.rows = []                        # (host time, sm_mhz, max_mhz, [reasons])
         self.window = None
+        self.source = None
 
     def __enter__(self):
+        try:
+            self.nvml = _Nvml(self.gpu)
+            self.source = "nvml, every 1 ms"
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi, every 100 ms"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
             t0 = time.perf_counter()
-            while not self.lines and time.perf_counter() - t0 < 5.0:     # sampler running before timing
+            while not self.rows and time.perf_counter() - t0 < 5.0:     # sampler running before timing
                 time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
 
+    def _poll(self):
+        while not self.stop:
+            r = self.nvml.sample()
+            if r is not None:
+                self.rows.append((time.perf_counter(),) + r)
+            time.sleep(self.period)
+
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
-            self.lines.append((time.perf_counter(), line.strip()))
+            p = [x.strip() for x in line.strip().split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                self.rows.append((time.perf_counter(), float(p[1]), float(p[2]),
+                                  [names[k] for k in range(4) if p[5 + k].lower() == "active"]))
+            except ValueError:
+                continue
 
     def mark(self, t_start: float, t_end: float) -> None:
         """Host-clock bounds of the timed region; samples outside are ignored
@@ -142,6 +203,7 @@ class ClockSampler:
         self.window = (t_start, t_end)
 
     def __exit__(self, *exc):
+        self.stop = True
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -150,29 +212,16 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        rows = []
-        lines = self.lines
+        rows = list(self.rows)
         if self.window is not None:
             t0, t1 = self.window
-            inside = [ln for t, ln in lines if t0 <= t <= t1]
-            after = [ln for t, ln in lines if t > t1][:1]
-            lines = inside + after
-        else:
-            lines = [ln for _, ln in lines]
-        for ln in lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                rows.append((float(p[1]), float(p[2]), p[5:9]))
-            except ValueError:
-                continue
+            rows = [r for r in rows if t0 <= r[0] <= t1] + [r for r in rows if r[0] > t1][:1]
         if not rows:
             return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({n for r in rows for n in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "sm_mhz_min": min(r[1] for r in rows), "reasons": reasons, "samples": len(rows),
+                "source": self.source}
 
 
 # ----------------------------------------------------------------------------
@@ -187,12 +236,26 @@ def oracle_sample_rows(P, step: int, target_nnz: int):
     return rows, nnz, stride
 
 
-def time_oracle_step(P, rows):
+def time_oracle_step(P, rows, keep=False):
+    """Seconds of one oracle SDDMM + SpMM over `rows`; with keep, also its
+    outputs (the SDDMM values, NaN outside the rows, and the SpMM rows)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals, rows=rows)
-    oracle.spmm(P.rowptr, P.colidx, P.B, P.vals, rows=rows)
-    return time.perf_counter() - t0
+    o = oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals, rows=rows)
+    c = oracle.spmm(P.rowptr, P.colidx, P.B, P.vals, rows=rows)
+    t = time.perf_counter() - t0
+    return (t, o, c) if keep else t
+
+
+def comp_err(got, ref, den) -> float:
+    """Componentwise error |got - ref| / (sum of the magnitudes of the terms);
+    outputs with a zero denominator must match exactly (inf otherwise)."""
+    got = np.asarray(got, np.float64)
+    d = np.abs(got - ref)
+    zero = den == 0
+    if np.any(zero) and np.any(d[zero] != 0):
+        return float("inf")
+    return float(np.max(np.where(zero, 0.0, d / np.where(zero, 1.0, den)), initial=0.0))
 
 
 def host_cores() -> int:
@@ -473,13 +536,52 @@ def main(args):
             events.append(ev)
         torch.cuda.synchronize(dev)
         clk.mark(wall0, time.perf_counter())
-        time.sleep(0.15)
+        time.sleep(0.05)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
+    clocks = clk.summary()
     t_sd = [e[0].elapsed_time(e[1]) for e in events]
     t_sp = [e[1].elapsed_time(e[2]) for e in events]
+
+    # the same step with BF16 factors (RNE casts of the same A, B, made once,
+    # untimed), FP32 accumulation and outputs: the precision comparison
+    bf = None
+    if dt == torch.float32 and not args.no_bf16:
+        Ab = spk.cast(A32, torch.bfloat16)
+        Bb = Ab if P.B is P.A else spk.cast(B32, torch.bfloat16)
+        out_b = torch.empty_like(out)
+        C_b = torch.empty_like(C)
+
+        def step_b():
+            spk.sddmm(S, Ab, Bb, out=out_b)
+            evb[1].record(stream)
+            spk.spmm(S, Bb, out=C_b)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            evb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step_b()
+        torch.cuda.synchronize(dev)
+        events_b = []
+        with ClockSampler(dev.index if world == 1 else local) as clk_b:
+            torch.cuda.synchronize(dev)
+            w0 = time.perf_counter()
+            for _ in range(args.steps):
+                flush.zero_()
+                evb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                evb[0].record(stream)
+                step_b()
+                evb[2].record(stream)
+                events_b.append(evb)
+            torch.cuda.synchronize(dev)
+            clk_b.mark(w0, time.perf_counter())
+            time.sleep(0.05)
+        tb_sd = [e[0].elapsed_time(e[1]) for e in events_b]
+        tb_sp = [e[1].elapsed_time(e[2]) for e in events_b]
+        Tb = max_over_ranks((sum(tb_sd) + sum(tb_sp)) / 1e3, dev)
+        bf = {"t_sd": tb_sd, "t_sp": tb_sp, "T": Tb, "clocks": clk_b.summary(), "out": out_b, "C": C_b}
     T = (sum(t_sd) + sum(t_sp)) / 1e3                      # seconds, this rank
     T = max_over_ranks(T, dev)
     flops_step = 2.0 * 2.0 * P.nnz * K
@@ -583,17 +685,31 @@ def main(args):
         "gpu_launches": 2 * args.steps,
         "wall_s": wall,
     }
+    if args.warmup != args.warmup_requested:
+        line["config"]["warmup_note"] = f"--warmup {args.warmup_requested} raised to {args.warmup} (at least 3)"
+    if bf is not None:
+        ab16 = algorithmic_bytes(P, 2)
+        bsd, bsp = statistics.mean(bf["t_sd"]), statistics.mean(bf["t_sp"])
+        line["kernels_bf16"] = {
+            "step_ms": 1e3 * bf["T"] / args.steps, "value": world * flops_step * args.steps / bf["T"] / 1e9,
+            "sddmm_ms": bsd, "spmm_ms": bsp,
+            "sddmm_gflops": 2.0 * P.nnz * K / (bsd / 1e3) / 1e9, "spmm_gflops": 2.0 * P.nnz * K / (bsp / 1e3) / 1e9,
+            "sddmm_algo_gbs": ab16["sddmm"] / (bsd / 1e3) / 1e9, "spmm_algo_gbs": ab16["spmm"] / (bsp / 1e3) / 1e9,
+            "clocks": bf["clocks"],
+            "note": "A, B cast to BF16 (round to nearest even) once, untimed; FP32 accumulation and outputs; "
+                    "same pattern, values, steps and L2 flushes as the FP32 line"}
+        line["bf16_over_f32"] = {"step": (T / args.steps) / (bf["T"] / args.steps), "sddmm": ms_sd / bsd,
+                                 "spmm": ms_sp / bsp, "note": "FP32 time / BF16 time (> 1: BF16 faster)"}
     if aux is not None:
         line["aux"] = aux
-    summ = clk.summary()
-    line["clocks"] = summ
+    line["clocks"] = clocks
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
         if P.vals is not None:      # FP64 values for the oracle (exact from FP32), converted once, untimed
             P.vals = P.vals.astype(np.float64)
         rows, nnz, stride = oracle_sample_rows(P, 0, args.cpu_nnz)
-        t = time_oracle_step(P, rows)
+        t, o_ref, c_ref = time_oracle_step(P, rows, keep=True)
         cores = min(host_cores(), 64)               # each thread holds an nnz-long output while it runs
         tc = time_oracle_step_threads(P, rows, cores) if cores > 1 else t
         line["cpu_baseline"] = {"value": 2.0 * 2.0 * nnz * K / tc / 1e9, "unit": "GFLOP/s", "cores": cores,
@@ -603,6 +719,25 @@ def main(args):
                                            + f" ({nnz:,} of {P.nnz:,} nonzeros), SDDMM + SpMM in the FP64 "
                                            f"oracle: {t:.1f} s on one host core, {tc:.2f} s on {cores} host "
                                            "threads (rows interleaved over the threads)")}
+        # what the timed oracle outputs say about the GPU's: componentwise
+        # error of the FP32 and BF16 steps against the FP64 oracle on the
+        # original FP32 inputs, on every 16th row of the sample (the
+        # denominators, sums of term magnitudes, come from the oracle too)
+        import oracle
+        er = rows[::16]
+        ent = np.concatenate([np.arange(P.rowptr[r], P.rowptr[r + 1]) for r in er]).astype(np.int64)
+        o_den = oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals, rows=er, absmode=True)[ent]
+        c_den = oracle.spmm(P.rowptr, P.colidx, P.B, P.vals, rows=er, absmode=True)
+        pos = np.searchsorted(rows, er)
+        par = {"rows": int(er.size), "nonzeros": int(ent.size),
+               "metric": "max |gpu - oracle| / sum of |terms| (oracle in FP64 on the FP32 inputs)",
+               "gates": {"f32": 1e-5, "bf16": 2e-2},
+               "f32": {"sddmm": comp_err(out.cpu().numpy()[ent], o_ref[ent], o_den),
+                       "spmm": comp_err(C.cpu().numpy()[er], c_ref[pos], c_den)}}
+        if bf is not None:
+            par["bf16"] = {"sddmm": comp_err(bf["out"].cpu().numpy()[ent], o_ref[ent], o_den),
+                           "spmm": comp_err(bf["C"].cpu().numpy()[er], c_ref[pos], c_den)}
+        line["cpu_baseline"]["parity"] = par
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -789,8 +924,11 @@ def parse():
     ap.add_argument("--ref-nnz", type=int, default=100_000, help="nonzeros per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the setup / SpMM^T / conversion measurements")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-factor timing of the FP32 line")
     a = ap.parse_args()
-    if a.warmup < 3:
+    a.warmup_requested = a.warmup
+    if a.warmup < 3:                # the timing rules ask for at least 3 warm-up steps; the line says so
+        print(f"bench.py: --warmup {a.warmup} raised to 3", file=sys.stderr)
         a.warmup = 3
     if a.chunk_work is None:
         # many small matrices with short rows: smaller chunks keep more warps busy

@@ -73,6 +73,8 @@ def lib():
                                          _i64, _p, _p, _p, _p]
             L.oracle_transpose.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
             L.oracle_merge_path.argtypes = [_i64, _p, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            L.oracle_coo_to_csr.argtypes = [_i64, _i64, _i64, _p, _p, _p, ctypes.c_int, _p, _p, _p,
+                                            ctypes.POINTER(_i64)]
             _lib = L
     return _lib
 
@@ -254,6 +256,25 @@ def transpose(rowptr, colidx, N):
     return colptr, rowidx, perm
 
 
+def coo_to_csr(rows, cols, M: int, N: int, vals=None, dedup: int = 1):
+    """COO -> CSR ordered by (row, column), ties in input order; dedup 0 keeps
+    every entry, 1 the first of each repeated (row, column), 2 one entry with
+    the repeats' values summed.  Returns (rowptr, colidx, vals float64 or
+    None)."""
+    rows = _c(rows, np.int32); cols = _c(cols, np.int32)
+    nnz = rows.size
+    rowptr = np.empty(M + 1, np.int32)
+    colidx = np.empty(nnz, np.int32)
+    out_v = np.empty(nnz) if vals is not None else None
+    n = _i64(0)
+    rc = lib().oracle_coo_to_csr(M, N, nnz, _ptr(rows), _ptr(cols), _ptr(_c(vals, np.float64)), int(dedup),
+                                 _ptr(rowptr), _ptr(colidx), _ptr(out_v), ctypes.byref(n))
+    if rc:
+        raise ValueError(f"oracle_coo_to_csr: bad input ({rc})")
+    k = n.value
+    return rowptr, colidx[:k].copy(), None if out_v is None else out_v[:k].copy()
+
+
 def merge_path(rowptr, d: int):
     """(rows finished, nonzeros consumed) after d steps of the merge path."""
     rowptr = _c(rowptr, np.int32)
@@ -303,13 +324,28 @@ def gnn_grad(rowptr, colidx, H, dY, vals=None, fmt=None):
     return g1 + g2 + g3
 
 
-def fusedmm_grad(rowptr, colidx, A, B, dY, vals=None, *, heads=1, scale=1.0, softmax=False, fmt=None):
+def fusedmm_grad(rowptr, colidx, A, B, dY, vals=None, *, heads=1, scale=1.0, softmax=False, fmt=None,
+                 absmode=False):
     """dA, dB of L = sum dY . Y for Y = fusedmm(S, A, B) (Sec. 2's SDDMM -> SpMM
     cascade), by the chain rule per head h over columns h*K/heads.. :
       e = scale s <a_i, b_j>,  w = e or softmax_j(e),  Y_i = sum_j w_ij b_j
       dw_ij = <dY_i, b_j>;  g = dw, or w (dw - sum_j' w_ij' dw_ij') with softmax
       c = scale g;  dA = (S.c) B;  dB = (S.c)^T A + W^T dY.
-    The weights come from this oracle's own FusedMM forward (scores, lse)."""
+    The weights come from this oracle's own FusedMM forward (scores, lse).
+
+    absmode=True returns the denominators of the componentwise error metric
+    instead: the same chain rule over the magnitudes of every term,
+      |dw|~ = sum_k |dY_ik||b_jk|,  |g|~ = |dw|~, or
+      |w|~ (|dw|~ + sum_j' |w_ij'|~ |dw_ij'|~) with softmax,
+      dA~ = sum_j |scale s_ij| |g_ij|~ |b_j|,
+      dB~ = sum_i |scale s_ij| |g_ij|~ |a_i| + sum_i |w_ij|~ |dY_i|,
+    where a softmax weight's magnitude is |w| (1 + |e|~) with
+    |e|~ = |scale| sum_k |s_ij a_ik b_jk|: a weight exp(e - lse) carries the
+    absolute rounding error of its exponent as a relative error.  Cancelling
+    sums (softmax score gradients sum to zero over a row) thus get the
+    magnitude of their terms, not of their result."""
+    if absmode:
+        return _fusedmm_grad_den(rowptr, colidx, A, B, dY, vals, heads=heads, scale=scale, softmax=softmax, fmt=fmt)
     rowptr = _c(rowptr, np.int32); colidx = _c(colidx, np.int32)
     M, K = A.shape
     N = B.shape[0]
@@ -332,4 +368,34 @@ def fusedmm_grad(rowptr, colidx, A, B, dY, vals=None, *, heads=1, scale=1.0, sof
         c = scale * g
         dA[:, sl] = spmm(rowptr, colidx, B[:, sl], vals, c, fmt_b=fmt)
         dB[:, sl] = spmm_t(rowptr, colidx, N, A[:, sl], vals, c, fmt_y=fmt) + spmm_t(rowptr, colidx, N, dY[:, sl], w)
+    return dA, dB
+
+
+def _fusedmm_grad_den(rowptr, colidx, A, B, dY, vals=None, *, heads=1, scale=1.0, softmax=False, fmt=None):
+    """Componentwise denominators of fusedmm_grad (see its absmode)."""
+    rowptr = _c(rowptr, np.int32); colidx = _c(colidx, np.int32)
+    M, K = A.shape
+    N = B.shape[0]
+    Kh = K // heads
+    rows = np.repeat(np.arange(M), np.diff(rowptr))
+    dY = np.asarray(dY, np.float64)
+    _, scores, lse = fusedmm(rowptr, colidx, A, B, vals, heads=heads, scale=scale, softmax=softmax,
+                             fmt_a=fmt, fmt_b=fmt)
+    dA = np.zeros((M, K))
+    dB = np.zeros((N, K))
+    for h in range(heads):
+        sl = slice(h * Kh, (h + 1) * Kh)
+        e_abs = abs(scale) * sddmm(rowptr, colidx, A[:, sl], B[:, sl], vals, None, fmt_a=fmt, fmt_b=fmt,
+                                   absmode=True)
+        w = np.exp(scores[h] - lse[rows, h]) * (1.0 + e_abs) if softmax else np.abs(scores[h])
+        dw = sddmm(rowptr, colidx, dY[:, sl], B[:, sl], None, None, fmt_b=fmt, absmode=True)
+        if softmax:
+            rowsum = np.bincount(rows, weights=w * dw, minlength=M)
+            g = w * (dw + rowsum[rows])
+        else:
+            g = dw
+        c = abs(scale) * g
+        dA[:, sl] = spmm(rowptr, colidx, B[:, sl], vals, c, fmt_b=fmt, absmode=True)
+        dB[:, sl] = (spmm_t(rowptr, colidx, N, A[:, sl], vals, c, fmt_y=fmt, absmode=True)
+                     + spmm_t(rowptr, colidx, N, dY[:, sl], w, absmode=True))
     return dA, dB

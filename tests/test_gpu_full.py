@@ -31,6 +31,27 @@ def _sample_cols(colidx, N, count, seed):
     return np.unique(np.concatenate([np.argsort(cdeg)[-6:], [0, N - 1], g.integers(0, N, count)])).astype(np.int64)
 
 
+def test_tiny_exact_config_all_entries(spk):
+    """The plain-method configuration exactly: Erdos-Renyi 4096 x 4096 with 16
+    distinct uniform columns per row (65,536 nonzeros), K = 32, values and
+    factors uniform [-1, 1] FP32, seed 0; SDDMM (Eq. 1), SpMM (Eq. 2) and
+    S^T A in the default launch configuration, every output element against
+    the oracle, componentwise at the FP32 tolerance."""
+    P = synth.tiny(seed=0)
+    assert (P.M, P.N, P.K, P.colidx.size) == (4096, 4096, 32, 65536)
+    S = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), torch.from_numpy(P.vals), device=DEV)
+    A, B = torch.from_numpy(P.A).to(DEV), torch.from_numpy(P.B).to(DEV)
+    out = spk.sddmm(S, A, B).cpu().numpy()
+    C = spk.spmm(S, B).cpu().numpy()
+    X = spk.spmm_t(S, A).cpu().numpy()
+    assert comp_err(out, oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals),
+                    oracle.sddmm(P.rowptr, P.colidx, P.A, P.B, P.vals, absmode=True)) <= TOL
+    assert comp_err(C, oracle.spmm(P.rowptr, P.colidx, P.B, P.vals),
+                    oracle.spmm(P.rowptr, P.colidx, P.B, P.vals, absmode=True)) <= TOL
+    assert comp_err(X, oracle.spmm_t(P.rowptr, P.colidx, P.N, P.A, P.vals),
+                    oracle.spmm_t(P.rowptr, P.colidx, P.N, P.A, P.vals, absmode=True)) <= TOL
+
+
 def test_rmat20_fp32(spk):
     P = synth.rmat_problem(20, 16, 64, seed=0)
     S = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), torch.from_numpy(P.vals), device=DEV)

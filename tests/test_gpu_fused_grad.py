@@ -1,7 +1,7 @@
 """Differentiable FusedMM on the GPU against the oracle's finite-difference
-pinned chain rule: the three elementwise kernels of the backward one by one
-(componentwise, FP32 tolerance), then dA and dB end to end for FP32 and BF16
-factors, with and without the row softmax, one and several heads."""
+pinned chain rule: the three elementwise kernels of the backward one by one,
+then dA and dB end to end for FP32 and BF16 factors, with and without the row
+softmax, one and several heads; every output componentwise."""
 import numpy as np
 import pytest
 import torch
@@ -12,16 +12,19 @@ from helpers import TOL, comp_err, edge_pattern, row_of
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
 
-# End-to-end gradients: FP32 throughout.  Each entry of dA / dB is a sum over
-# a row (or column) of products whose factors (scores, weights, dw, the row
-# term) each carry a few FP32 roundings relative to their magnitudes.  With
-# softmax the score gradients of a row sum to zero, so entries can cancel far
-# below the magnitudes of their terms: the check is normwise over the matrix,
-# max |got - ref| <= GRAD_TOL * max |ref|, where GRAD_TOL = 1e-4 leaves a
-# decade over rows of up to 2,500 terms while any dropped or mis-signed term
-# moves the result at the 1e-1 level.
-GRAD_TOL = 1e-4
-GRAD_TOL_16 = 2.0 ** -8 + GRAD_TOL     # plus one BF16 rounding of dA, dB
+# End-to-end gradients, componentwise like every other output: each entry of
+# dA / dB is compared with the oracle's chain rule relative to the sum of the
+# magnitudes of the terms that form it (oracle.fusedmm_grad with absmode: the
+# same chain rule over |A|, |B|, |dY|, |w|, |dw|, the softmax row term as
+# sum |w| |dw|, and a softmax weight's magnitude widened by its exponent's).
+# Softmax score gradients sum to zero over a row, so an entry can cancel far
+# below its terms; the denominator does not cancel.  FP32: 1e-5.  BF16 dH =
+# dA + dB: each written in BF16 and summed in BF16, three roundings of at
+# most 2^-8 of quantities bounded by the denominator, two of them disjoint.
+GRAD_TOL = TOL
+GRAD_TOL_16 = 2 * 2.0 ** -8 + TOL
+# The normwise check below is kept as a second, coarser view.
+NORM_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -131,8 +134,12 @@ def test_fusedmm_grad_f32(spk, heads, softmax):
     assert comp_err(Y.detach().cpu().numpy(), Yr, Ya) <= TOL
     Y.backward(torch.from_numpy(dY).to(DEV))
     dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, heads=heads, scale=scale, softmax=softmax)
-    assert _normwise(tA.grad.cpu().numpy(), dA) <= GRAD_TOL
-    assert _normwise(tB.grad.cpu().numpy(), dB) <= GRAD_TOL
+    dA_den, dB_den = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, heads=heads, scale=scale, softmax=softmax,
+                                         absmode=True)
+    assert comp_err(tA.grad.cpu().numpy(), dA, dA_den) <= GRAD_TOL
+    assert comp_err(tB.grad.cpu().numpy(), dB, dB_den) <= GRAD_TOL
+    assert _normwise(tA.grad.cpu().numpy(), dA) <= NORM_TOL
+    assert _normwise(tB.grad.cpu().numpy(), dB) <= NORM_TOL
     empty = np.flatnonzero(np.diff(rp) == 0)
     assert np.all(tA.grad.cpu().numpy()[empty] == 0.0)
 
@@ -148,8 +155,11 @@ def test_fusedmm_grad_bf16_shared_operand(spk, softmax):
     Y = spk.autograd.fusedmm(S, tH, tH, S.vals, heads=heads, scale=0.25, softmax=softmax)
     Y.backward(torch.from_numpy(dY).to(DEV))
     dA, dB = oracle.fusedmm_grad(rp, ci, Hq, Hq, dY, vals, heads=heads, scale=0.25, softmax=softmax, fmt="bf16")
+    dA_den, dB_den = oracle.fusedmm_grad(rp, ci, Hq, Hq, dY, vals, heads=heads, scale=0.25, softmax=softmax,
+                                         fmt="bf16", absmode=True)
     assert tH.grad.dtype == torch.bfloat16
-    assert _normwise(tH.grad.float().cpu().numpy(), dA + dB) <= 2 * GRAD_TOL_16
+    assert comp_err(tH.grad.float().cpu().numpy(), dA + dB, dA_den + dB_den) <= GRAD_TOL_16
+    assert _normwise(tH.grad.float().cpu().numpy(), dA + dB) <= 2 * (2.0 ** -8 + NORM_TOL)
 
 
 def test_fusedmm_grad_matches_unfused_composition(spk):
@@ -163,5 +173,11 @@ def test_fusedmm_grad_matches_unfused_composition(spk):
     a2 = torch.from_numpy(A).to(DEV).requires_grad_(); b2 = torch.from_numpy(B).to(DEV).requires_grad_()
     e = spk.autograd.sddmm(S, a2, b2, S.vals * 0.5)
     spk.autograd.spmm(S, b2, e).backward(torch.from_numpy(dY).to(DEV))
-    for x, y in ((a1.grad, a2.grad), (b1.grad, b2.grad)):
-        assert _normwise(x.cpu().numpy(), y.double().cpu().numpy()) <= GRAD_TOL
+    dA_den, dB_den = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, scale=0.5, absmode=True)
+    dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, scale=0.5)
+    for x, y, ref, den in ((a1.grad, a2.grad, dA, dA_den), (b1.grad, b2.grad, dB, dB_den)):
+        # both against the oracle, and to each other at twice that
+        assert comp_err(x.cpu().numpy(), ref, den) <= GRAD_TOL
+        assert comp_err(y.cpu().numpy(), ref, den) <= GRAD_TOL
+        assert comp_err(x.cpu().numpy(), y.double().cpu().numpy(), den) <= 2 * GRAD_TOL
+        assert _normwise(x.cpu().numpy(), y.double().cpu().numpy()) <= NORM_TOL

@@ -533,3 +533,91 @@ def test_fusedmm_gradient_against_dense_autograd(heads, softmax):
     gA, gB = torch.autograd.grad((torch.from_numpy(dY) * Y).sum(), (tA, tB))
     np.testing.assert_allclose(dA, gA.numpy(), rtol=1e-10, atol=1e-12)
     np.testing.assert_allclose(dB, gB.numpy(), rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("heads,softmax", [(1, False), (2, False), (1, True), (3, True)])
+def test_fusedmm_gradient_denominators(heads, softmax):
+    """The componentwise denominators of the FusedMM gradient (the chain rule
+    over magnitudes) against a dense masked formulation of the same magnitudes,
+    and two properties that hold for any input: they bound |dA|, |dB|, and with
+    every factor nonnegative and no softmax (no cancellation) they equal them."""
+    M, N, K = 15, 12, 4 * heads
+    rp, ci, vals, A, B = random_case(M, N, K, 0.3, seed=70 + heads + 3 * softmax)
+    A = A.astype(np.float64); B = B.astype(np.float64); vals = vals.astype(np.float64)
+    dY = np.random.default_rng(71).standard_normal((M, K))
+    scale = -0.6
+    kw = dict(heads=heads, scale=scale, softmax=softmax)
+    dA, dB = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, **kw)
+    dA_den, dB_den = oracle.fusedmm_grad(rp, ci, A, B, dY, vals, absmode=True, **kw)
+    assert np.all(dA_den >= np.abs(dA) * (1 - 1e-12)) and np.all(dB_den >= np.abs(dB) * (1 - 1e-12))
+    # dense masked magnitudes, written out per head
+    S_abs = np.abs(dense(rp, ci, vals, M, N))
+    mask = dense(rp, ci, None, M, N) > 0
+    D = K // heads
+    eA, eB = np.zeros((M, K)), np.zeros((N, K))
+    for h in range(heads):
+        sl = slice(h * D, (h + 1) * D)
+        Ah, Bh, dYh = A[:, sl], B[:, sl], dY[:, sl]
+        E = scale * dense(rp, ci, vals, M, N) * (Ah @ Bh.T)
+        if softmax:
+            Em = np.where(mask, E, -np.inf)
+            mx = np.max(Em, axis=1, keepdims=True)
+            P = np.where(mask, np.exp(Em - np.where(np.isfinite(mx), mx, 0.0)), 0.0)
+            tot = P.sum(axis=1, keepdims=True)
+            W = np.where(tot > 0, P / np.where(tot > 0, tot, 1.0), 0.0)
+            W = W * (1.0 + abs(scale) * S_abs * (np.abs(Ah) @ np.abs(Bh).T))
+        else:
+            W = np.where(mask, np.abs(E), 0.0)
+        dw = np.where(mask, np.abs(dYh) @ np.abs(Bh).T, 0.0)
+        g = W * (dw + (W * dw).sum(axis=1, keepdims=True)) if softmax else dw
+        C = abs(scale) * S_abs * g
+        eA[:, sl] = C @ np.abs(Bh)
+        eB[:, sl] = C.T @ np.abs(Ah) + W.T @ np.abs(dYh)
+    np.testing.assert_allclose(dA_den, eA, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(dB_den, eB, rtol=1e-12, atol=1e-14)
+    if not softmax:
+        # nonnegative factors and a positive scale: nothing cancels
+        Ap, Bp, dYp, vp = np.abs(A), np.abs(B), np.abs(dY), np.abs(vals)
+        kp = dict(heads=heads, scale=0.6, softmax=False)
+        pA, pB = oracle.fusedmm_grad(rp, ci, Ap, Bp, dYp, vp, **kp)
+        qA, qB = oracle.fusedmm_grad(rp, ci, Ap, Bp, dYp, vp, absmode=True, **kp)
+        np.testing.assert_allclose(qA, pA, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(qB, pB, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("dedup", [0, 1, 2])
+def test_coo_to_csr_against_numpy(dedup):
+    """COO -> CSR against numpy's stable lexsort (order by row, then column,
+    ties in input order), np.unique for the repeats, and np.add.at for their
+    summed values; the de-duplicated pattern equals the generators' CSR."""
+    g = np.random.default_rng(90 + dedup)
+    M, N, n = 57, 43, 900
+    rows = g.integers(0, M, n).astype(np.int32)
+    cols = g.integers(0, N, n).astype(np.int32)
+    rows[:40] = rows[40:80]; cols[:40] = cols[40:80]            # plenty of repeats
+    rows[5] = M - 1; cols[5] = N - 1
+    vals = g.uniform(-1, 1, n)
+    rp, ci, v = oracle.coo_to_csr(rows, cols, M, N, vals, dedup)
+    order = np.lexsort((np.arange(n), cols, rows))
+    r_s, c_s, v_s = rows[order], cols[order], vals[order]
+    if dedup == 0:
+        exp_r, exp_c, exp_v = r_s, c_s, v_s
+    else:
+        first = np.ones(n, bool)
+        first[1:] = (r_s[1:] != r_s[:-1]) | (c_s[1:] != c_s[:-1])
+        exp_r, exp_c = r_s[first], c_s[first]
+        if dedup == 1:
+            exp_v = v_s[first]
+        else:
+            exp_v = np.zeros(first.sum())
+            np.add.at(exp_v, np.cumsum(first) - 1, v_s)
+        srp, sci = synth.csr_from_coo(rows, cols, M, N)
+        assert np.array_equal(srp, rp) and np.array_equal(sci, ci)
+    assert np.array_equal(ci, exp_c)
+    assert np.array_equal(rp, np.searchsorted(exp_r, np.arange(M + 1), side="left").astype(np.int32))
+    np.testing.assert_allclose(v, exp_v, rtol=1e-14, atol=1e-15)
+    # empty input and an index out of range
+    rp0, ci0, _ = oracle.coo_to_csr(np.zeros(0, np.int32), np.zeros(0, np.int32), 3, 2, None, dedup)
+    assert np.array_equal(rp0, [0, 0, 0, 0]) and ci0.size == 0
+    with pytest.raises(ValueError):
+        oracle.coo_to_csr(np.array([0], np.int32), np.array([N], np.int32), M, N, None, dedup)
