@@ -108,6 +108,26 @@ spk_status spk_csr_destroy(spk_csr S);
  * launched; the outcome is in d_report. */
 spk_status spk_csr_validate(spk_csr S, int32_t* d_report, void* stream);
 
+/* COO -> CSR on the device.  The paper states S by its nonzeros s_ij, i.e.
+ * by coordinates (Sec. 3.1: S is M x N); the kernels take CSR.  rows[nnz],
+ * cols[nnz] (device int32) and optional vals[nnz] (device FP32, NULL = no
+ * values) are ordered by (row, column), ties in input order.  dedup: 0 keeps
+ * every entry (repeats become independent entries, which SpMM sums); 1 keeps
+ * the first entry, in input order, of each repeated (row, column); 2 keeps one
+ * entry whose value is the FP32 sum of the repeats' values in input order.
+ * Outputs (device, caller-owned): rowptr[M+1]; colidx and vals_out (NULL = not
+ * wanted; all ones when vals is NULL) of at least nnz entries, of which the
+ * first *nnz_out are written (colidx 16-byte aligned if it is then wrapped by
+ * spk_csr_create).  temp: >= spk_coo_to_csr_size bytes, 256-byte aligned,
+ * scratch for this call only.  Synchronises `stream` once, at the end, to
+ * return *nnz_out (host) and to report a coordinate outside the matrix as
+ * SPK_ERR_INDEX (the outputs are then undefined; nothing is read or written
+ * out of bounds).  Not capturable in a CUDA graph (it synchronises). */
+spk_status spk_coo_to_csr_size(int64_t M, int64_t N, int64_t nnz, size_t* temp_bytes);
+spk_status spk_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                          const float* vals, int32_t dedup, int32_t* rowptr, int32_t* colidx, float* vals_out,
+                          int64_t* nnz_out, void* temp, size_t temp_bytes, void* stream);
+
 /* ------------------------------------------------------------ schedule -- */
 /* The balanced schedule cuts the merged sequence of (row ends, nonzeros) into
  * chunks of about `chunk_work` items (merge-path partition), snapping each cut
@@ -164,12 +184,16 @@ spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
  * workspace; the caller still passes the inputs and C.  Neither the caller nor
  * the library allocates: no cudaMalloc, cudaFree or allocating library call.
  * Arguments, layouts and results are those of spk_spmm.
- *  - Limit: spk_schedule_info's npieces x K x 4 must not exceed
+ *  - Limit: with the balanced schedule (the default when one is attached),
+ *    spk_schedule_info's npieces x K x 4 must not exceed
  *    SPK_STATIC_SCRATCH_BYTES; larger calls return SPK_ERR_WORKSPACE before
- *    any launch (use spk_spmm then).
- *  - Set-up: the first call on a device (the current one) looks up the
- *    scratch's device address with cudaGetSymbolAddress; make that first call
- *    before any stream capture.
+ *    any launch (use spk_spmm then).  Row-split calls (tune.variant = 1) use
+ *    no scratch and have no limit.
+ *  - Set-up: the first call in a CUDA context of a device (the current one)
+ *    looks up the scratch's device address with cudaGetSymbolAddress and
+ *    keeps it for that context; make that first call before any stream
+ *    capture.  cudaDeviceReset ends the context, so the first call after it
+ *    looks the address up again (and again belongs before any capture).
  *  - Sharing: every call on a device uses the same scratch, which keeps the
  *    last call's contents.  Nothing in it needs to start at zero, so it is
  *    never cleared.  Calls that overlap on the GPU (other streams, other host

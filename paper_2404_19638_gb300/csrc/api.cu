@@ -224,6 +224,48 @@ extern "C" spk_status spk_merge_path_points(spk_csr S, int32_t W, int64_t n, int
 }
 
 // ----------------------------------------------------------------------------
+// COO -> CSR
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_coo_to_csr_size(int64_t M, int64_t N, int64_t nnz, size_t* temp_bytes)
+{
+    REQUIRE(temp_bytes, SPK_ERR_ARG, "spk_coo_to_csr_size: temp_bytes is NULL");
+    REQUIRE(M >= 0 && N >= 0 && nnz >= 0, SPK_ERR_ARG, "spk_coo_to_csr_size: negative size");
+    REQUIRE(M < INT32_MAX && N < INT32_MAX && nnz < INT32_MAX, SPK_ERR_UNSUPPORTED,
+            "spk_coo_to_csr_size: sizes must be below 2^31-1 (int32 indices)");
+    *temp_bytes = coo_temp_bytes(M, N, nnz);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                                     const float* vals, int32_t dedup, int32_t* rowptr, int32_t* colidx,
+                                     float* vals_out, int64_t* nnz_out, void* temp, size_t temp_bytes, void* stream)
+{
+    REQUIRE(nnz_out, SPK_ERR_ARG, "spk_coo_to_csr: nnz_out is NULL");
+    *nnz_out = 0;
+    REQUIRE(M >= 0 && N >= 0 && nnz >= 0, SPK_ERR_ARG, "spk_coo_to_csr: negative size");
+    REQUIRE(M < INT32_MAX && N < INT32_MAX && nnz < INT32_MAX, SPK_ERR_UNSUPPORTED,
+            "spk_coo_to_csr: sizes must be below 2^31-1 (int32 indices)");
+    REQUIRE(dedup >= 0 && dedup <= 2, SPK_ERR_ARG, "spk_coo_to_csr: dedup must be 0, 1 or 2");
+    REQUIRE(rowptr, SPK_ERR_ARG, "spk_coo_to_csr: rowptr is NULL");
+    REQUIRE(nnz == 0 || (rows && cols && colidx), SPK_ERR_ARG, "spk_coo_to_csr: NULL coordinate array");
+    REQUIRE(nnz == 0 || N > 0, SPK_ERR_SHAPE, "spk_coo_to_csr: entries in a matrix with no columns");
+    const size_t need = coo_temp_bytes(M, N, nnz);
+    REQUIRE(temp && temp_bytes >= need, SPK_ERR_WORKSPACE, "spk_coo_to_csr: temp has %zu bytes, needs %zu",
+            temp ? temp_bytes : (size_t)0, need);
+    REQUIRE((reinterpret_cast<uintptr_t>(temp) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "spk_coo_to_csr: temp must be 256-byte aligned");
+    int32_t bad = -1;
+    int64_t n = 0;
+    cudaError_t e = coo_to_csr(M, N, nnz, rows, cols, vals, dedup, rowptr, colidx, vals_out, &n, &bad,
+                               reinterpret_cast<char*>(temp), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_coo_to_csr");
+    REQUIRE(bad < 0, SPK_ERR_INDEX, "spk_coo_to_csr: entry %d has a coordinate outside the %lld x %lld matrix", bad,
+            (long long)M, (long long)N);
+    *nnz_out = n;
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
 // Kernel shape selection
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
@@ -533,13 +575,51 @@ extern "C" spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t sof
 // Carry slots of spk_spmm_static.  A file-scope device array: every GPU that
 // loads the library holds SPK_STATIC_SCRATCH_BYTES of it until the process
 // exits.  In host code `g_static_scratch` is only a stand-in for the symbol;
-// its device address comes from cudaGetSymbolAddress, taken once per device
-// (with that device current) on the first spk_spmm_static call there.
+// its device address comes from cudaGetSymbolAddress, taken with the device
+// current on the first spk_spmm_static call in each CUDA context of that
+// device.  The cache is keyed on the context's unique ID, so after
+// cudaDeviceReset (which destroys the primary context; the module, and with
+// it the array, is loaded again in the next one) the address is taken anew.
 static __device__ __align__(256) float g_static_scratch[SPK_STATIC_SCRATCH_BYTES / sizeof(float)];
 
 static constexpr int kMaxStaticDevices = 64;
 static std::mutex g_static_mu;
-static void* g_static_addr[kMaxStaticDevices];
+struct StaticAddr {
+    unsigned long long ctx_id;   // unique ID of the context the address belongs to (0 = none yet)
+    void* addr;
+};
+static StaticAddr g_static_addr[kMaxStaticDevices];
+
+// Driver entry points for the current context and its ID, fetched through the
+// runtime (the library does not link the driver library itself).
+typedef int (*ctx_get_current_fn)(void** ctx);
+typedef int (*ctx_get_id_fn)(void* ctx, unsigned long long* id);
+
+static spk_status current_context_id(unsigned long long* id)
+{
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: driver entry point cuCtxGetCurrent");
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: driver entry point cuCtxGetId");
+        REQUIRE(q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2, SPK_ERR_CUDA,
+                "spk_spmm_static: the driver does not provide cuCtxGetCurrent / cuCtxGetId");
+        get_current = reinterpret_cast<ctx_get_current_fn>(f1);
+        get_id = reinterpret_cast<ctx_get_id_fn>(f2);
+    }
+    void* ctx = nullptr;
+    int r = get_current(&ctx);
+    REQUIRE(r == 0, SPK_ERR_CUDA, "spk_spmm_static: cuCtxGetCurrent failed (%d)", r);
+    REQUIRE(ctx, SPK_ERR_STATE, "spk_spmm_static: no CUDA context is current on this thread");
+    r = get_id(ctx, id);
+    REQUIRE(r == 0, SPK_ERR_CUDA, "spk_spmm_static: cuCtxGetId failed (%d)", r);
+    return SPK_OK;
+}
 
 static spk_status static_scratch_address(void** out)
 {
@@ -548,16 +628,31 @@ static spk_status static_scratch_address(void** out)
     if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: cudaGetDevice");
     REQUIRE(dev >= 0 && dev < kMaxStaticDevices, SPK_ERR_UNSUPPORTED,
             "spk_spmm_static: device ordinal %d is beyond the %d supported", dev, kMaxStaticDevices);
+    // cudaGetSymbolAddress also makes the device's primary context current if
+    // no context is yet, so look the symbol up before asking for the context.
+    void* p = nullptr;
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
+    unsigned long long id = 0;
+    const bool cached = g_static_addr[dev].addr != nullptr;
+    if (!cached) {
         e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: cudaGetSymbolAddress");
-        REQUIRE(p && (reinterpret_cast<uintptr_t>(p) & 255u) == 0, SPK_ERR_CUDA,
-                "spk_spmm_static: scratch symbol address is NULL or misaligned");
-        g_static_addr[dev] = p;
     }
-    *out = g_static_addr[dev];
+    spk_status st = current_context_id(&id);
+    if (st != SPK_OK) return st;
+    if (cached && g_static_addr[dev].ctx_id == id) {
+        *out = g_static_addr[dev].addr;
+        return SPK_OK;
+    }
+    if (cached) {                 // another context than the cached address belongs to
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_static: cudaGetSymbolAddress");
+    }
+    REQUIRE(p && (reinterpret_cast<uintptr_t>(p) & 255u) == 0, SPK_ERR_CUDA,
+            "spk_spmm_static: scratch symbol address is NULL or misaligned");
+    g_static_addr[dev].ctx_id = id;
+    g_static_addr[dev].addr = p;
+    *out = p;
     return SPK_OK;
 }
 
@@ -568,7 +663,10 @@ extern "C" spk_status spk_spmm_static(spk_csr S, const float* vals, const float*
 {
     REQUIRE(S, SPK_ERR_ARG, "spk_spmm_static: S is NULL");
     REQUIRE(K >= 1, SPK_ERR_SHAPE, "spk_spmm_static: K must be >= 1 (got %d)", K);
-    const size_t need = S->has_sched ? (size_t)S->npieces * (size_t)K * 4 : 0;
+    // Only the balanced schedule's split rows use carry slots: a row-split
+    // call (tune.variant = 1) needs no scratch whatever K is.
+    const int variant = (tune && tune->variant) ? tune->variant : (S->has_sched ? 2 : 1);
+    const size_t need = (variant >= 2 && S->has_sched) ? (size_t)S->npieces * (size_t)K * 4 : 0;
     REQUIRE(need <= (size_t)SPK_STATIC_SCRATCH_BYTES, SPK_ERR_WORKSPACE,
             "spk_spmm_static: %lld split-row pieces x K = %d need %zu bytes of scratch, above the %zu bytes "
             "held by the library (use spk_spmm with a caller workspace)",
