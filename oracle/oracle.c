@@ -16,6 +16,7 @@
  *           cascaded into SpMM), per head, optionally row-softmax weights
  * plus the bookkeeping the GPU path needs a reference for:
  *   - a stable counting-sort transpose (CSR -> CSC with slot permutation),
+ *   - COO -> CSR by two stable counting sorts, with duplicate handling,
  *   - the merge-path split point of the (row ends, nonzeros) merge, by walking,
  *   - number-format encoders / decoders written from the format definitions
  *     (IEEE binary16, bfloat16 = top half of binary32, OCP FP8 E4M3),
@@ -392,4 +393,60 @@ void oracle_merge_path(int64_t M, const int32_t* rowptr, int64_t d, int64_t* r_o
     }
     *r_out = r;
     *e_out = e;
+}
+
+/* ------------------------------------------------------------------------- */
+/* COO -> CSR.  S given by coordinates (Sec. 3.1: the nonzeros s_ij of an    */
+/* M x N matrix) is put in row-major order: entries ordered by (row, column),*/
+/* ties in input order, by two stable counting sorts (column, then row).     */
+/* dedup 0 keeps every entry; 1 keeps the first entry (in input order) of    */
+/* each repeated (row, column); 2 keeps one entry whose value is the sum of  */
+/* the repeated entries' values (in double).  vals / vals_out may be NULL.   */
+/* Writes rowptr[M+1], colidx / vals_out[nnz_out]; returns 1 on an index out */
+/* of range, 3 on allocation failure.                                        */
+/* ------------------------------------------------------------------------- */
+int oracle_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                      const double* vals, int dedup, int32_t* rowptr, int32_t* colidx, double* vals_out,
+                      int64_t* nnz_out)
+{
+    int64_t* by_col = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t* cnt = (int64_t*)calloc((size_t)((M > N ? M : N) + 1), sizeof(int64_t));
+    if (!by_col || !order || !cnt) { free(by_col); free(order); free(cnt); return 3; }
+    for (int64_t e = 0; e < nnz; ++e)
+        if (rows[e] < 0 || rows[e] >= M || cols[e] < 0 || cols[e] >= N) {
+            free(by_col); free(order); free(cnt);
+            return 1;
+        }
+    /* stable counting sort by column */
+    for (int64_t e = 0; e < nnz; ++e) cnt[cols[e] + 1]++;
+    for (int64_t j = 0; j < N; ++j) cnt[j + 1] += cnt[j];
+    for (int64_t e = 0; e < nnz; ++e) by_col[cnt[cols[e]]++] = e;
+    /* stable counting sort of that order by row */
+    memset(cnt, 0, sizeof(int64_t) * (size_t)((M > N ? M : N) + 1));
+    for (int64_t e = 0; e < nnz; ++e) cnt[rows[e] + 1]++;
+    for (int64_t i = 0; i < M; ++i) cnt[i + 1] += cnt[i];
+    for (int64_t q = 0; q < nnz; ++q) {
+        int64_t e = by_col[q];
+        order[cnt[rows[e]]++] = e;
+    }
+    /* emit, merging repeats */
+    int64_t n = 0;
+    for (int64_t i = 0; i <= M; ++i) rowptr[i] = 0;
+    for (int64_t q = 0; q < nnz; ++q) {
+        int64_t e = order[q];
+        int repeat = q > 0 && rows[order[q - 1]] == rows[e] && cols[order[q - 1]] == cols[e];
+        if (dedup && repeat) {
+            if (dedup == 2 && vals && vals_out) vals_out[n - 1] += vals[e];
+            continue;
+        }
+        colidx[n] = cols[e];
+        if (vals_out) vals_out[n] = vals ? vals[e] : 1.0;
+        rowptr[rows[e] + 1]++;
+        n++;
+    }
+    for (int64_t i = 0; i < M; ++i) rowptr[i + 1] += rowptr[i];
+    *nnz_out = n;
+    free(by_col); free(order); free(cnt);
+    return 0;
 }

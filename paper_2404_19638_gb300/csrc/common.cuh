@@ -415,6 +415,22 @@ cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const fl
                                 cudaStream_t s);
 cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
                             char* storage, char* temp, const TplanLayout& L, cudaStream_t s);
+// Stable LSD radix sort of n int32 keys (8 bits per pass, `passes` passes over
+// the low bits) carrying int32 values (NULL = the identity 0..n-1); the result
+// lands in k0/v0 or k1/v1 (pointers returned; keys/vals themselves when n = 0
+// or passes = 0).  hist: radix_hist_bytes(n); scan_tmp: scan_temp_bytes of the
+// histogram's entries (radix_tiles(n) * 256).
+int radix_passes(int64_t range);          // passes that cover keys in [0, range)
+int64_t radix_tiles(int64_t n);
+size_t radix_hist_bytes(int64_t n);
+cudaError_t radix_sort_i32(const int32_t* keys, const int32_t* vals, int64_t n, int passes, int32_t* k0, int32_t* k1,
+                           int32_t* v0, int32_t* v1, int32_t* hist, void* scan_tmp, const int32_t** keys_out,
+                           const int32_t** vals_out, cudaStream_t s);
+// COO -> CSR (coo.cu)
+size_t coo_temp_bytes(int64_t M, int64_t N, int64_t nnz);
+cudaError_t coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols, const float* vals,
+                       int dedup, int32_t* rowptr, int32_t* colidx, float* vals_out, int64_t* nnz_out,
+                       int32_t* first_bad, char* temp, cudaStream_t s);
 
 cudaError_t launch_cast(const float* x, int64_t n, int dt, void* out, cudaStream_t s);
 cudaError_t launch_quant_e4m3(const float* X, int64_t M, int64_t K, int64_t ldx, uint8_t* Q, int64_t ldq,

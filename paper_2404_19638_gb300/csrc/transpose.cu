@@ -29,11 +29,8 @@ TplanLayout tplan_layout(int64_t M, int64_t N, int64_t nnz, int32_t W)
     L.sched = off;  off += L.sl.total;
     L.total = off;
 
-    int bits = 0;
-    while (bits < 31 && (int64_t(1) << bits) < N) ++bits;
-    L.passes = (bits + 7) / 8;
-    L.nblocks = (nnz + RX_TILE - 1) / RX_TILE;
-    if (L.nblocks < 1) L.nblocks = 1;
+    L.passes = radix_passes(N);
+    L.nblocks = radix_tiles(nnz);
     size_t t = 0;
     L.keys0 = t; t += align256((size_t)nnz * 4 + 4);
     L.keys1 = t; t += align256((size_t)nnz * 4 + 4);
@@ -161,6 +158,38 @@ cudaError_t launch_permute_vals(const int32_t* perm, const float* vals, const fl
     return cudaGetLastError();
 }
 
+int radix_passes(int64_t range)
+{
+    int bits = 0;
+    while (bits < 31 && (int64_t(1) << bits) < range) ++bits;
+    return (bits + 7) / 8;
+}
+
+int64_t radix_tiles(int64_t n) { return n < 1 ? 1 : (n + RX_TILE - 1) / RX_TILE; }
+
+size_t radix_hist_bytes(int64_t n) { return align256((size_t)radix_tiles(n) * RX_DIGITS * 4); }
+
+cudaError_t radix_sort_i32(const int32_t* keys, const int32_t* vals, int64_t n, int passes, int32_t* k0, int32_t* k1,
+                           int32_t* v0, int32_t* v1, int32_t* hist, void* scan_tmp, const int32_t** keys_out,
+                           const int32_t** vals_out, cudaStream_t s)
+{
+    const int64_t nblocks = radix_tiles(n);
+    const int32_t* kin = keys;
+    const int32_t* vin = vals;
+    for (int p = 0; n > 0 && p < passes; ++p) {
+        int32_t* kout = (p & 1) ? k1 : k0;
+        int32_t* vout = (p & 1) ? v1 : v0;
+        k_rx_hist<<<(unsigned)nblocks, RX_THREADS, 0, s>>>(kin, n, 8 * p, nblocks, hist);
+        cudaError_t err = scan_exclusive_i32(hist, hist, nblocks * RX_DIGITS, scan_tmp, s);
+        if (err != cudaSuccess) return err;
+        k_rx_scatter<<<(unsigned)nblocks, RX_THREADS, 0, s>>>(kin, vin, n, 8 * p, nblocks, hist, kout, vout);
+        kin = kout; vin = vout;
+    }
+    *keys_out = kin;
+    *vals_out = vin;
+    return cudaGetLastError();
+}
+
 cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
                             char* storage, char* temp, const TplanLayout& L, cudaStream_t s)
 {
@@ -174,22 +203,12 @@ cudaError_t build_transpose(const int32_t* rowptr, const int32_t* colidx, int64_
     int32_t* hist = reinterpret_cast<int32_t*>(temp + L.hist);
     cudaError_t err;
 
-    const int32_t* kin = colidx;
-    const int32_t* vin = nullptr;
     const int32_t* sorted_keys = colidx;
     const int32_t* sorted_vals = nullptr;
     if (nnz > 0) {
-        for (int p = 0; p < L.passes; ++p) {
-            int32_t* kout = (p & 1) ? k1 : k0;
-            int32_t* vout = (p & 1) ? v1 : v0;
-            k_rx_hist<<<(unsigned)L.nblocks, RX_THREADS, 0, s>>>(kin, nnz, 8 * p, L.nblocks, hist);
-            err = scan_exclusive_i32(hist, hist, L.nblocks * RX_DIGITS, temp + L.scan_tmp, s);
-            if (err != cudaSuccess) return err;
-            k_rx_scatter<<<(unsigned)L.nblocks, RX_THREADS, 0, s>>>(kin, vin, nnz, 8 * p, L.nblocks, hist, kout, vout);
-            kin = kout; vin = vout;
-        }
-        sorted_keys = kin;
-        sorted_vals = vin;
+        err = radix_sort_i32(colidx, nullptr, nnz, L.passes, k0, k1, v0, v1, hist, temp + L.scan_tmp, &sorted_keys,
+                             &sorted_vals, s);
+        if (err != cudaSuccess) return err;
     }
     // perm: sorted values (identity when no pass ran, i.e. N <= 1)
     if (nnz > 0) {

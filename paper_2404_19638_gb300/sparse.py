@@ -33,6 +33,40 @@ def _as_i32(x, device) -> torch.Tensor:
     return x.contiguous()
 
 
+DEDUP = {"keep": 0, "first": 1, "sum": 2}
+
+
+def coo_to_csr(rows, cols, shape, vals=None, *, dedup: str = "first", device="cuda"):
+    """Coordinates -> CSR on the device (spk_coo_to_csr): entries ordered by
+    (row, column), ties in input order; repeated (row, column) entries kept
+    ("keep"), reduced to the first ("first") or summed ("sum").  Returns
+    (rowptr, colidx, vals or None) as device tensors."""
+    device = torch.device(device)
+    if device.type == "cuda" and device.index is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    M, N = int(shape[0]), int(shape[1])
+    r = _as_i32(rows, device)
+    c = _as_i32(cols, device)
+    if r.numel() != c.numel():
+        raise ValueError("rows and cols must have the same length")
+    n = int(r.numel())
+    v = None if vals is None else torch.as_tensor(vals, dtype=torch.float32).to(device).contiguous()
+    tb = ctypes.c_size_t()
+    check(lib().spk_coo_to_csr_size(M, N, n, ctypes.byref(tb)), "spk_coo_to_csr_size")
+    temp = _buffer(tb.value, device)
+    rowptr = torch.empty(M + 1, dtype=torch.int32, device=device)
+    colidx = torch.empty(max(n, 1), dtype=torch.int32, device=device)
+    vout = None if v is None else torch.empty(max(n, 1), dtype=torch.float32, device=device)
+    nout = ctypes.c_int64()
+    with torch.cuda.device(device):
+        check(lib().spk_coo_to_csr(M, N, n, r.data_ptr() if n else None, c.data_ptr() if n else None,
+                                   None if v is None else v.data_ptr(), DEDUP[dedup], rowptr.data_ptr(),
+                                   colidx.data_ptr(), None if vout is None else vout.data_ptr(), ctypes.byref(nout),
+                                   temp.data_ptr(), temp.numel(), _stream(device)), "spk_coo_to_csr")
+    k = nout.value
+    return rowptr, colidx[:k].clone(), None if vout is None else vout[:k].clone()
+
+
 class CSR:
     """Pattern of an M x N sparse matrix S (Sec. 3.1), optionally with values.
 
@@ -61,6 +95,12 @@ class CSR:
         self._tplan = None
         if schedule:
             self.build_schedule(chunk_work)
+
+    @classmethod
+    def from_coo(cls, rows, cols, shape, vals=None, *, dedup: str = "first", device="cuda", **kw) -> "CSR":
+        """A pattern (and values) given by coordinates, converted on the device."""
+        rp, ci, v = coo_to_csr(rows, cols, shape, vals, dedup=dedup, device=device)
+        return cls(rp, ci, shape, v, device=device, **kw)
 
     # ---------------------------------------------------------------- setup
     @property
