@@ -128,6 +128,47 @@ spk_status spk_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows
                           const float* vals, int32_t dedup, int32_t* rowptr, int32_t* colidx, float* vals_out,
                           int64_t* nnz_out, void* temp, size_t temp_bytes, void* stream);
 
+/* ------------------------------------------------------ row relabelling -- */
+/* Locality reordering.  The paper localises indices before its Compute phase
+ * (Sec. 5.2: a processor renumbers the rows and columns it holds and drops
+ * empty ones); on one GPU the counterpart relabels S's rows so that rows
+ * gathering the same B rows run close together and share L2 lines.
+ *
+ * spk_reorder_rows writes perm[M] (device int32): perm[p] = the original row
+ * placed at position p, ties kept in the original order:
+ *   SPK_ORDER_DEGREE          most entries first (a device sort);
+ *   SPK_ORDER_LEADING_COLUMN  smallest column first, rows without entries last
+ *                             (a device sort; restores a band whose rows were
+ *                             shuffled);
+ *   SPK_ORDER_RCM             reverse Cuthill-McKee (Cuthill & McKee 1969,
+ *                             reversed after George 1971) on the symmetric
+ *                             graph of a square pattern, edge i - j for every
+ *                             stored (i, j), i != j; components start from the
+ *                             unvisited vertex of smallest (degree, index) and
+ *                             neighbours are queued by (degree, index).  Runs
+ *                             on the host: copies the pattern out and the order
+ *                             back, synchronising `stream` (temp unused).
+ * spk_permute_pattern builds the relabelled pattern S' (row p of S' = row
+ * perm[p] of S, same columns in the same order, original column ids):
+ * rowptr_out[M+1], colidx_out[nnz], emap[nnz] = the slot in S of each slot of
+ * S'.  S' is an ordinary CSR pattern (wrap it with spk_csr_create); with
+ * A' = A[perm] its SDDMM and SpMM equal those of S up to the order of rows and
+ * entries: out = scatter of out' through emap, C = scatter of C' through perm.
+ * spk_permute_rows: Y[p] = X[perm[p]] (scatter 0) or Y[perm[p]] = X[p]
+ * (scatter 1), M rows of K elements of dtype dt, leading dimensions ldx, ldy.
+ * spk_permute_values: y[i] = x[map[i]] (scatter 0) or y[map[i]] = x[i] (1).
+ * temp (the two sorts and spk_permute_pattern): >= spk_reorder_size bytes,
+ * 256-byte aligned.  Outputs must not overlap inputs. */
+enum { SPK_ORDER_DEGREE = 1, SPK_ORDER_LEADING_COLUMN = 2, SPK_ORDER_RCM = 3 };
+spk_status spk_reorder_size(spk_csr S, size_t* temp_bytes);
+spk_status spk_reorder_rows(spk_csr S, int32_t order, int32_t* perm, void* temp, size_t temp_bytes, void* stream);
+spk_status spk_permute_pattern(spk_csr S, const int32_t* perm, int32_t* rowptr_out, int32_t* colidx_out,
+                               int32_t* emap, void* temp, size_t temp_bytes, void* stream);
+spk_status spk_permute_rows(const void* X, int64_t ldx, spk_dtype dt, int64_t M, int32_t K, const int32_t* perm,
+                            int32_t scatter, void* Y, int64_t ldy, void* stream);
+spk_status spk_permute_values(const float* x, const int32_t* map, int64_t n, int32_t scatter, float* y,
+                              void* stream);
+
 /* ------------------------------------------------------------ schedule -- */
 /* The balanced schedule cuts the merged sequence of (row ends, nonzeros) into
  * chunks of about `chunk_work` items (merge-path partition), snapping each cut

@@ -73,6 +73,7 @@ def lib():
                                          _i64, _p, _p, _p, _p]
             L.oracle_transpose.argtypes = [_i64, _i64, _p, _p, _p, _p, _p]
             L.oracle_merge_path.argtypes = [_i64, _p, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+            L.oracle_rcm.argtypes = [_i64, _p, _p, _p]
             L.oracle_coo_to_csr.argtypes = [_i64, _i64, _i64, _p, _p, _p, ctypes.c_int, _p, _p, _p,
                                             ctypes.POINTER(_i64)]
             _lib = L
@@ -273,6 +274,38 @@ def coo_to_csr(rows, cols, M: int, N: int, vals=None, dedup: int = 1):
         raise ValueError(f"oracle_coo_to_csr: bad input ({rc})")
     k = n.value
     return rowptr, colidx[:k].copy(), None if out_v is None else out_v[:k].copy()
+
+
+def rcm(rowptr, colidx):
+    """Reverse Cuthill-McKee order of a square pattern: perm[p] = the row placed
+    at position p (ties by (degree, index), components from the unvisited
+    vertex of smallest (degree, index))."""
+    rowptr = _c(rowptr, np.int32); colidx = _c(colidx, np.int32)
+    M = rowptr.size - 1
+    perm = np.empty(M, np.int32)
+    rc = lib().oracle_rcm(M, _ptr(rowptr), _ptr(colidx), _ptr(perm))
+    if rc:
+        raise ValueError(f"oracle_rcm: bad input ({rc})")
+    return perm
+
+
+def row_order(rowptr, colidx, N: int, kind: str):
+    """Row relabelling by a stable sort: "degree" (most nonzeros first) or
+    "leading" (smallest column first; rows without entries last).  Ties keep
+    the original order.  perm[p] = the row placed at position p."""
+    rowptr = np.asarray(rowptr, np.int64)
+    deg = np.diff(rowptr)
+    M = deg.size
+    if kind == "degree":
+        key = -deg
+    elif kind == "leading":
+        key = np.full(M, N, np.int64)
+        for i in range(M):
+            if deg[i]:
+                key[i] = int(np.min(np.asarray(colidx)[rowptr[i]:rowptr[i + 1]]))
+    else:
+        raise ValueError(kind)
+    return np.argsort(key, kind="stable").astype(np.int32)
 
 
 def merge_path(rowptr, d: int):

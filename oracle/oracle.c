@@ -17,6 +17,9 @@
  * plus the bookkeeping the GPU path needs a reference for:
  *   - a stable counting-sort transpose (CSR -> CSC with slot permutation),
  *   - COO -> CSR by two stable counting sorts, with duplicate handling,
+ *   - the reverse Cuthill-McKee order of a square pattern (a row relabelling
+ *     for locality; not the paper's, the single-GPU stand-in for its
+ *     localisation of indices),
  *   - the merge-path split point of the (row ends, nonzeros) merge, by walking,
  *   - number-format encoders / decoders written from the format definitions
  *     (IEEE binary16, bfloat16 = top half of binary32, OCP FP8 E4M3),
@@ -448,5 +451,73 @@ int oracle_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, co
     for (int64_t i = 0; i < M; ++i) rowptr[i + 1] += rowptr[i];
     *nnz_out = n;
     free(by_col); free(order); free(cnt);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reverse Cuthill-McKee order of a square pattern (Cuthill & McKee 1969,    */
+/* reversed as George 1971 proposed), on the symmetric graph with an edge    */
+/* i - j for every stored (i, j), i != j (repeats count in the degree).      */
+/* Components are started, in turn, from the unvisited vertex of smallest    */
+/* (degree, index); a vertex's unvisited neighbours are queued by (degree,   */
+/* index).  perm[p] = vertex at position p of the reversed visiting order.   */
+/* ------------------------------------------------------------------------- */
+static const int64_t* g_rcm_deg;
+static int rcm_cmp(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    if (g_rcm_deg[x] != g_rcm_deg[y]) return g_rcm_deg[x] < g_rcm_deg[y] ? -1 : 1;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oracle_rcm(int64_t M, const int32_t* rowptr, const int32_t* colidx, int32_t* perm)
+{
+    int64_t nnz = rowptr[M];
+    int64_t* deg = (int64_t*)calloc((size_t)M + 1, sizeof(int64_t));
+    int64_t* start = (int64_t*)calloc((size_t)M + 1, sizeof(int64_t));
+    int64_t* adj = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * nnz + 1));
+    int64_t* fill = (int64_t*)calloc((size_t)M + 1, sizeof(int64_t));
+    int64_t* byd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M + 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M + 1));
+    char* seen = (char*)calloc((size_t)M + 1, 1);
+    if (!deg || !start || !adj || !fill || !byd || !order || !seen) {
+        free(deg); free(start); free(adj); free(fill); free(byd); free(order); free(seen);
+        return 3;
+    }
+    for (int64_t i = 0; i < M; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t j = colidx[e];
+            if (j < 0 || j >= M) { free(deg); free(start); free(adj); free(fill); free(byd); free(order); free(seen); return 2; }
+            if (j != i) { deg[i]++; deg[j]++; }
+        }
+    for (int64_t i = 0; i < M; ++i) start[i + 1] = start[i] + deg[i];
+    for (int64_t i = 0; i < M; ++i)
+        for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            int64_t j = colidx[e];
+            if (j == i) continue;
+            adj[start[i] + fill[i]++] = j;
+            adj[start[j] + fill[j]++] = i;
+        }
+    g_rcm_deg = deg;
+    for (int64_t i = 0; i < M; ++i) byd[i] = i;
+    qsort(byd, (size_t)M, sizeof(int64_t), rcm_cmp);
+    int64_t head = 0, tail = 0, next_start = 0;
+    while (tail < M) {
+        while (seen[byd[next_start]]) next_start++;
+        int64_t s = byd[next_start];
+        seen[s] = 1;
+        order[tail++] = s;
+        while (head < tail) {
+            int64_t v = order[head++];
+            int64_t first = tail;
+            for (int64_t q = start[v]; q < start[v + 1]; ++q) {
+                int64_t w = adj[q];
+                if (!seen[w]) { seen[w] = 1; order[tail++] = w; }
+            }
+            qsort(order + first, (size_t)(tail - first), sizeof(int64_t), rcm_cmp);
+        }
+    }
+    for (int64_t p = 0; p < M; ++p) perm[p] = (int32_t)order[M - 1 - p];
+    free(deg); free(start); free(adj); free(fill); free(byd); free(order); free(seen);
     return 0;
 }

@@ -2,6 +2,7 @@
 
     S = CSR(rowptr, colidx, (M, N), vals)        # pattern + balanced schedule
     S = CSR.from_coo(rows, cols, (M, N), vals)   # the same from coordinates (sorted on the device)
+    R = Reordering(S, "rcm")                      # row relabelling for locality: R.S, R.gather_rows(A), ...
     out = sddmm(S, A, B)                          # Eq. 1, FP32 per nonzero
     C = spmm(S, B)                                # Eq. 2
     X = spmm_t(S, Y)                              # S^T Y via the transpose plan
@@ -12,7 +13,7 @@ PyTorch supplies device memory and streams.  There is no CPU fallback: the
 first call raises if libspk.so was not built.
 """
 from .binding import SpkError, Tune, library_path
-from .sparse import CSR, TransposePlan, DEFAULT_CHUNK_WORK, coo_to_csr
+from .sparse import CSR, TransposePlan, DEFAULT_CHUNK_WORK, coo_to_csr, Reordering
 from .ops import sddmm, spmm, spmm_t, fusedmm, cast, quantize_e4m3_rows
 from . import autograd
 from .batch import Batch, Item, OP_SDDMM, OP_SPMM
@@ -20,4 +21,4 @@ from .autotune import Autotuner
 
 __all__ = ["CSR", "TransposePlan", "sddmm", "spmm", "spmm_t", "fusedmm", "cast", "quantize_e4m3_rows", "autograd",
            "Batch", "Item", "OP_SDDMM", "OP_SPMM", "Autotuner", "SpkError", "Tune", "library_path", "DEFAULT_CHUNK_WORK",
-           "coo_to_csr"]
+           "coo_to_csr", "Reordering"]

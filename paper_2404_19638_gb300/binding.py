@@ -59,6 +59,11 @@ _PROTOS = {
     "spk_csr_validate": (ctypes.c_int, [_vp, _vp, _vp]),
     "spk_coo_to_csr_size": (ctypes.c_int, [_i64, _i64, _i64, _P(_sz)]),
     "spk_coo_to_csr": (ctypes.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _P(_i64), _vp, _sz, _vp]),
+    "spk_reorder_size": (ctypes.c_int, [_vp, _P(_sz)]),
+    "spk_reorder_rows": (ctypes.c_int, [_vp, _i32, _vp, _vp, _sz, _vp]),
+    "spk_permute_pattern": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "spk_permute_rows": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _i64, _i32, _vp, _i32, _vp, _i64, _vp]),
+    "spk_permute_values": (ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp]),
     "spk_schedule_size": (ctypes.c_int, [_vp, _i32, _P(_sz)]),
     "spk_schedule_build": (ctypes.c_int, [_vp, _i32, _vp, _sz, _vp]),
     "spk_schedule_info": (ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i32)]),

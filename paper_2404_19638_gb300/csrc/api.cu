@@ -266,6 +266,80 @@ extern "C" spk_status spk_coo_to_csr(int64_t M, int64_t N, int64_t nnz, const in
 }
 
 // ----------------------------------------------------------------------------
+// Row relabelling for locality
+// ----------------------------------------------------------------------------
+extern "C" spk_status spk_reorder_size(spk_csr S, size_t* temp_bytes)
+{
+    REQUIRE(S && temp_bytes, SPK_ERR_ARG, "spk_reorder_size: NULL argument");
+    *temp_bytes = reorder_temp_bytes(S->M);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_reorder_rows(spk_csr S, int32_t order, int32_t* perm, void* temp, size_t temp_bytes,
+                                       void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_reorder_rows: S is NULL");
+    REQUIRE(order >= SPK_ORDER_DEGREE && order <= SPK_ORDER_RCM, SPK_ERR_ARG,
+            "spk_reorder_rows: order must be SPK_ORDER_DEGREE, SPK_ORDER_LEADING_COLUMN or SPK_ORDER_RCM");
+    REQUIRE(order != SPK_ORDER_RCM || S->M == S->N, SPK_ERR_SHAPE,
+            "spk_reorder_rows: reverse Cuthill-McKee needs a square pattern (got %lld x %lld)", (long long)S->M,
+            (long long)S->N);
+    REQUIRE(S->M == 0 || perm, SPK_ERR_ARG, "spk_reorder_rows: perm is NULL");
+    const size_t need = reorder_temp_bytes(S->M);
+    REQUIRE(order == SPK_ORDER_RCM || (temp && temp_bytes >= need), SPK_ERR_WORKSPACE,
+            "spk_reorder_rows: temp has %zu bytes, needs %zu", temp ? temp_bytes : (size_t)0, need);
+    REQUIRE(order == SPK_ORDER_RCM || (reinterpret_cast<uintptr_t>(temp) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "spk_reorder_rows: temp must be 256-byte aligned");
+    int hs = 0;
+    cudaError_t e = row_order(S->rowptr, S->colidx, S->M, S->N, S->nnz, order, perm, reinterpret_cast<char*>(temp),
+                              &hs, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_reorder_rows");
+    REQUIRE(hs == 0, SPK_ERR_INDEX, "spk_reorder_rows: a column index is outside the square pattern");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_permute_pattern(spk_csr S, const int32_t* perm, int32_t* rowptr_out, int32_t* colidx_out,
+                                          int32_t* emap, void* temp, size_t temp_bytes, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_permute_pattern: S is NULL");
+    REQUIRE(rowptr_out && (S->M == 0 || perm) && (S->nnz == 0 || (colidx_out && emap)), SPK_ERR_ARG,
+            "spk_permute_pattern: NULL array");
+    const size_t need = reorder_temp_bytes(S->M);
+    REQUIRE(temp && temp_bytes >= need, SPK_ERR_WORKSPACE, "spk_permute_pattern: temp has %zu bytes, needs %zu",
+            temp ? temp_bytes : (size_t)0, need);
+    REQUIRE((reinterpret_cast<uintptr_t>(temp) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "spk_permute_pattern: temp must be 256-byte aligned");
+    cudaError_t e = permute_pattern(S->rowptr, S->colidx, S->M, perm, rowptr_out, colidx_out, emap,
+                                    reinterpret_cast<char*>(temp), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_permute_pattern");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_permute_rows(const void* X, int64_t ldx, spk_dtype dt, int64_t M, int32_t K,
+                                       const int32_t* perm, int32_t scatter, void* Y, int64_t ldy, void* stream)
+{
+    REQUIRE(valid_dt(dt), SPK_ERR_DTYPE, "spk_permute_rows: unknown dtype");
+    REQUIRE(M >= 0 && K >= 0 && ldx >= K && ldy >= K, SPK_ERR_SHAPE, "spk_permute_rows: bad shape");
+    REQUIRE(scatter == 0 || scatter == 1, SPK_ERR_ARG, "spk_permute_rows: scatter must be 0 or 1");
+    REQUIRE(M == 0 || K == 0 || (X && Y && perm), SPK_ERR_ARG, "spk_permute_rows: NULL array");
+    REQUIRE(X != Y || M == 0 || K == 0, SPK_ERR_ARG, "spk_permute_rows: X and Y must not be the same buffer");
+    const int64_t b = dt_bytes(dt);
+    cudaError_t e = permute_rows(X, ldx * b, M, (int64_t)K * b, perm, scatter, Y, ldy * b, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_permute_rows");
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_permute_values(const float* x, const int32_t* map, int64_t n, int32_t scatter, float* y,
+                                         void* stream)
+{
+    REQUIRE(n >= 0 && (scatter == 0 || scatter == 1), SPK_ERR_ARG, "spk_permute_values: bad argument");
+    REQUIRE(n == 0 || (x && map && y && x != y), SPK_ERR_ARG, "spk_permute_values: NULL or aliased array");
+    cudaError_t e = permute_values(x, map, n, scatter, y, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_permute_values");
+    return SPK_OK;
+}
+
+// ----------------------------------------------------------------------------
 // Kernel shape selection
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };

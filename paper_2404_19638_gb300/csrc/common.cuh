@@ -426,6 +426,15 @@ size_t radix_hist_bytes(int64_t n);
 cudaError_t radix_sort_i32(const int32_t* keys, const int32_t* vals, int64_t n, int passes, int32_t* k0, int32_t* k1,
                            int32_t* v0, int32_t* v1, int32_t* hist, void* scan_tmp, const int32_t** keys_out,
                            const int32_t** vals_out, cudaStream_t s);
+// Row relabelling (reorder.cu)
+size_t reorder_temp_bytes(int64_t M);
+cudaError_t row_order(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz, int kind,
+                      int32_t* perm, char* temp, int* host_status, cudaStream_t s);
+cudaError_t permute_pattern(const int32_t* rowptr, const int32_t* colidx, int64_t M, const int32_t* perm,
+                            int32_t* rowptr2, int32_t* colidx2, int32_t* emap, char* temp, cudaStream_t s);
+cudaError_t permute_rows(const void* X, int64_t ldx_b, int64_t M, int64_t bytes, const int32_t* perm, int scatter,
+                         void* Y, int64_t ldy_b, cudaStream_t s);
+cudaError_t permute_values(const float* x, const int32_t* map, int64_t n, int scatter, float* y, cudaStream_t s);
 // COO -> CSR (coo.cu)
 size_t coo_temp_bytes(int64_t M, int64_t N, int64_t nnz);
 cudaError_t coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols, const float* vals,

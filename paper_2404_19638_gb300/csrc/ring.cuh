@@ -206,7 +206,10 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
             const int d = b % D;
             const int eg = tb0 + b * WB + grp * U;
             uint4* sB = ringB + d * U * NV * 32 + lane;
-            const bool fast = (eg >= e0) && (eg + U <= e1) && (row[0] == row[U - 1]);
+            // one decision for the whole warp: a batch that could take the
+            // fast path is also right on the general one, and lock-stepped
+            // groups running the two paths one after the other cost both
+            const bool fast = __all_sync(0xffffffffu, (eg >= e0) && (eg + U <= e1) && (row[0] == row[U - 1]));
             if (fast) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -284,7 +287,7 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
         const int meta = mmeta[d * GPW + grp];
         const uint4* sB = ringB + d * U * NV * 32 + lane;
         float p[U];
-        if (meta & 1) {
+        if (meta & 1) {                                  // issued on the fast path (a warp-wide decision)
             if (meta & 2) {                              // new row from nonzero 0 on: its A slice is in the ring
 #pragma unroll
                 for (int t = 0; t < NV; ++t)

@@ -259,3 +259,74 @@ class TransposePlan:
 
 
 __all__ = ["CSR", "TransposePlan", "SpkError", "DEFAULT_CHUNK_WORK"]
+
+
+ORDERS = {"degree": 1, "leading": 2, "rcm": 3}
+_DT = {torch.float32: 0, torch.bfloat16: 1, torch.float16: 2, torch.uint8: 3}
+
+
+class Reordering:
+    """Row relabelling of a pattern for locality (spk_reorder_rows,
+    spk_permute_pattern): ``perm[p]`` is the original row placed at position
+    p; ``S`` is the relabelled pattern (same column ids) carrying the values
+    in its slot order; ``emap[e']`` is the original slot of each of its entries.
+
+    With A' = gather_rows(A), SDDMM(S', A', B) = gather_values(SDDMM(S, A, B))
+    and SpMM(S', B) = gather_rows(SpMM(S, B)); scatter_values / scatter_rows
+    map results back to the original indices."""
+
+    def __init__(self, S: CSR, order: str = "rcm", *, chunk_work: int = DEFAULT_CHUNK_WORK):
+        self.order = order
+        self.M, self.N, self.nnz = S.M, S.N, S.nnz
+        self.device = S.device
+        tb = ctypes.c_size_t()
+        check(lib().spk_reorder_size(S.handle, ctypes.byref(tb)), "spk_reorder_size")
+        temp = _buffer(tb.value, S.device)
+        self.perm = torch.empty(max(S.M, 1), dtype=torch.int32, device=S.device)[:S.M]
+        with torch.cuda.device(S.device):
+            check(lib().spk_reorder_rows(S.handle, ORDERS[order], self.perm.data_ptr() if S.M else None,
+                                         temp.data_ptr(), temp.numel(), _stream(S.device)), "spk_reorder_rows")
+            rp = torch.empty(S.M + 1, dtype=torch.int32, device=S.device)
+            ci = torch.empty(max(S.nnz, 1), dtype=torch.int32, device=S.device)
+            self.emap = torch.empty(max(S.nnz, 1), dtype=torch.int32, device=S.device)
+            check(lib().spk_permute_pattern(S.handle, self.perm.data_ptr() if S.M else None, rp.data_ptr(),
+                                            ci.data_ptr(), self.emap.data_ptr(), temp.data_ptr(), temp.numel(),
+                                            _stream(S.device)), "spk_permute_pattern")
+        self.emap = self.emap[:S.nnz]
+        vals = None if S.vals is None else self.gather_values(S.vals)
+        self.S = CSR(rp, ci[:S.nnz], (S.M, S.N), vals, device=S.device, chunk_work=chunk_work)
+
+    def _rows(self, X: torch.Tensor, scatter: int) -> torch.Tensor:
+        if X.dim() != 2 or X.size(0) != self.M or X.stride(1) != 1 or X.device != self.device:
+            raise ValueError("expected an M x K row-major CUDA tensor")
+        Y = torch.empty((self.M, X.size(1)), dtype=X.dtype, device=X.device)
+        check(lib().spk_permute_rows(X.data_ptr(), X.stride(0), _DT[X.dtype], self.M, X.size(1),
+                                     self.perm.data_ptr() if self.M else None, scatter, Y.data_ptr(), Y.stride(0),
+                                     _stream(X.device)), "spk_permute_rows")
+        return Y
+
+    def gather_rows(self, X: torch.Tensor) -> torch.Tensor:
+        """X'[p] = X[perm[p]] (an M-row operand or result into the new order)."""
+        return self._rows(X, 0)
+
+    def scatter_rows(self, Xp: torch.Tensor) -> torch.Tensor:
+        """X[perm[p]] = X'[p] (back to the original row order)."""
+        return self._rows(Xp, 1)
+
+    def _vals(self, x: torch.Tensor, scatter: int) -> torch.Tensor:
+        if x.dtype != torch.float32 or x.numel() != self.nnz or x.device != self.device:
+            raise ValueError("expected nnz FP32 values on the pattern's device")
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        check(lib().spk_permute_values(x.data_ptr(), self.emap.data_ptr() if self.nnz else None, self.nnz, scatter,
+                                       y.data_ptr(), _stream(x.device)), "spk_permute_values")
+        return y
+
+    def gather_values(self, x: torch.Tensor) -> torch.Tensor:
+        """Per-entry values of S into the slot order of S'."""
+        return self._vals(x, 0)
+
+    def scatter_values(self, xp: torch.Tensor) -> torch.Tensor:
+        """Per-entry results on S' back to the slot order of S."""
+        return self._vals(xp, 1)
+

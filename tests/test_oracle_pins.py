@@ -621,3 +621,54 @@ def test_coo_to_csr_against_numpy(dedup):
     assert np.array_equal(rp0, [0, 0, 0, 0]) and ci0.size == 0
     with pytest.raises(ValueError):
         oracle.coo_to_csr(np.array([0], np.int32), np.array([N], np.int32), M, N, None, dedup)
+
+
+def test_row_orders_and_rcm_properties():
+    """Row relabellings: the stable sorts by their definitions, and reverse
+    Cuthill-McKee by what it is for — bandwidth 1 on a relabelled path, the
+    grid width on a relabelled grid, each component contiguous, the reversed
+    order ending at a vertex of smallest degree."""
+    g = np.random.default_rng(81)
+    rp, ci = synth.csr_from_coo(g.integers(0, 40, 300), g.integers(0, 55, 300), 40, 55)
+    deg = np.diff(rp)
+    p = oracle.row_order(rp, ci, 55, "degree")
+    assert sorted(p.tolist()) == list(range(40)) and np.all(np.diff(deg[p]) <= 0)
+    for a, b in zip(p[:-1], p[1:]):
+        assert deg[a] > deg[b] or a < b                       # ties in the original order
+    q = oracle.row_order(rp, ci, 55, "leading")
+    lead = np.array([ci[rp[i]:rp[i + 1]].min() if deg[i] else 55 for i in range(40)])
+    assert np.all(np.diff(lead[q]) >= 0)
+
+    def relabelled(edges, n, seed):
+        lab = np.random.default_rng(seed).permutation(n)
+        r = np.concatenate([lab[edges[:, 0]], lab[edges[:, 1]]])
+        c = np.concatenate([lab[edges[:, 1]], lab[edges[:, 0]]])
+        return synth.csr_from_coo(r, c, n, n)
+
+    def bandwidth(rp, ci, perm):
+        inv = np.empty_like(perm); inv[perm] = np.arange(perm.size)
+        rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+        return int(np.max(np.abs(inv[rows] - inv[ci])))
+
+    path = np.array([[i, i + 1] for i in range(59)])
+    rp, ci = relabelled(path, 60, 1)
+    perm = oracle.rcm(rp, ci)
+    assert sorted(perm.tolist()) == list(range(60)) and bandwidth(rp, ci, perm) == 1
+    w = 9
+    grid = np.array([[r * w + c, r * w + c + 1] for r in range(12) for c in range(w - 1)]
+                    + [[r * w + c, (r + 1) * w + c] for r in range(11) for c in range(w)])
+    rp, ci = relabelled(grid, 12 * w, 2)
+    perm = oracle.rcm(rp, ci)
+    assert bandwidth(rp, ci, perm) <= w + 1
+    # two components (a path and a triangle) and an isolated vertex
+    edges = np.array([[0, 1], [1, 2], [2, 3], [4, 5], [5, 6], [6, 4]])
+    rp, ci = relabelled(edges, 8, 3)
+    perm = oracle.rcm(rp, ci)
+    comp = {}
+    lab = np.random.default_rng(3).permutation(8)
+    for v in range(8):
+        comp[lab[v]] = 0 if v < 4 else (1 if v < 7 else 2)
+    seq = [comp[v] for v in perm]
+    assert len([k for k in range(1, 8) if seq[k] != seq[k - 1]]) == 2      # each component contiguous
+    deg = np.diff(rp)
+    assert deg[perm[-1]] == deg.min()
