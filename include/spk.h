@@ -70,7 +70,9 @@ typedef struct spk_tune {
     int32_t variant;        /* 0 default, 1 row-split (one lane group per row),
                                2 balanced chunks (merge-path schedule, needs spk_schedule_build),
                                  gathered rows staged in shared memory where the path supports it,
-                               3 balanced chunks, gathered rows held in registers */
+                               3 balanced chunks, gathered rows held in registers,
+                               4 as 2, SpMM in the ring's lean form where it applies
+                                 (one vector per lane, K covered by whole blocks) */
     int32_t group_lanes;    /* lanes that share one row of the dense factor: 4, 8, 16, 32 */
     int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
     int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
@@ -81,6 +83,7 @@ typedef struct spk_tune {
 typedef struct spk_csr_s* spk_csr;       /* pattern of S (+ its schedule)      */
 typedef struct spk_tplan_s* spk_tplan;   /* transpose plan of a pattern        */
 typedef struct spk_batch_s* spk_batch;   /* batched persistent launch          */
+typedef struct spk_tcplan_s* spk_tcplan; /* dense tiles for the tensor cores   */
 
 /* ---------------------------------------------------------------- misc -- */
 const char* spk_status_string(spk_status s);
@@ -290,6 +293,42 @@ spk_status spk_fused_rowdot(int64_t M, int32_t K, int32_t heads, const float* dY
                             int64_t ldy, float* rowdot, void* stream);
 spk_status spk_fused_score_grad(spk_csr S, int32_t heads, int32_t softmax, float scale, const float* vals,
                                 const float* w, const float* dw, const float* rowdot, float* c, void* stream);
+
+/* --------------------------------------------- tensor-core dense tiles -- */
+/* Where a 128-row x 64-column tile of S holds many entries, its SDDMM (Eq. 1)
+ * is a real contraction: the tile's A panel (128 x K) and B tile (64 x K) are
+ * read once and multiplied whole on the tensor cores (tcgen05, FP32
+ * accumulation in tensor memory), then sampled at the tile's entries.
+ * spk_tc_plan_build finds the tiles (panel = row / 128, column tile =
+ * column / 64) holding at least `threshold` entries (0 = 1024, an eighth of
+ * the tile) and builds the remainder pattern (every other entry, each row in
+ * order) with its balanced schedule (chunk_work as in spk_schedule_build).
+ * storage holds the plan for its lifetime (size from spk_tc_plan_size, an
+ * upper bound); temp is scratch for the build.  Synchronises `stream`.
+ * spk_tc_plan_arrays: device views for tests — the tiles as int32 quadruples
+ * {panel, column tile, first entry, entries}, the slot in S of each
+ * dense-tile entry, the remainder's rowptr (M+1), colidx and slot in S of
+ * each entry, and the status word (1 after a tensor-core wait ran out).
+ *
+ * spk_tc_sddmm: out = SDDMM(S, A, B) with vals (NULL = ones), A (M x K) and
+ * B (N x K) BF16, 16-byte aligned with 16-byte row strides, K a multiple of
+ * 16 up to 256: the remainder through spk_sddmm (into the workspace, >=
+ * spk_tc_sddmm_workspace_size bytes, then scaled into place), the dense
+ * tiles on the tensor cores.  Results are within FP32 accumulation error of
+ * spk_sddmm's (a different summation order). */
+spk_status spk_tc_plan_size(spk_csr S, int32_t threshold, int32_t chunk_work, size_t* storage_bytes,
+                            size_t* temp_bytes);
+spk_status spk_tc_plan_build(spk_csr S, int32_t threshold, int32_t chunk_work, void* storage, size_t storage_bytes,
+                             void* temp, size_t temp_bytes, spk_tcplan* out, void* stream);
+spk_status spk_tc_plan_info(spk_tcplan P, int64_t* tiles, int64_t* dense_nnz, int64_t* rest_nnz);
+spk_status spk_tc_plan_arrays(spk_tcplan P, const int32_t** tiles, const int32_t** ent_slot,
+                              const int32_t** rest_rowptr, const int32_t** rest_colidx, const int32_t** rest_emap,
+                              int32_t** status);
+spk_status spk_tc_plan_destroy(spk_tcplan P);
+spk_status spk_tc_sddmm_workspace_size(spk_tcplan P, size_t* bytes);
+spk_status spk_tc_sddmm(spk_tcplan P, const float* vals, spk_dtype dt, const void* A, int64_t lda, const void* B,
+                        int64_t ldb, int32_t K, float* out, void* workspace, size_t ws_bytes, const spk_tune* tune,
+                        void* stream);
 
 /* ----------------------------------------------------- transpose plan -- */
 /* The CSC of S by a stable device radix sort on the column index: colptr[N+1],

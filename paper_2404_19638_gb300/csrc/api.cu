@@ -376,12 +376,12 @@ static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16
 static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, const spk_tune* t, Launch* L)
 {
     const int variant = (t && t->variant) ? t->variant : (S->has_sched ? 2 : 1);
-    REQUIRE(variant >= 1 && variant <= 3, SPK_ERR_ARG, "tune.variant %d is not 0, 1, 2 or 3", variant);
+    REQUIRE(variant >= 1 && variant <= 4, SPK_ERR_ARG, "tune.variant %d is not 0, 1, 2, 3 or 4", variant);
     REQUIRE(variant == 1 || S->has_sched, SPK_ERR_STATE, "balanced variant needs spk_schedule_build first");
     const int vecn = vec ? vec_elems(dtb) : 1;
     const int nvec = K / vecn;
     int G, NV, U;
-    const bool half16 = vec && (variant == 2) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
+    const bool half16 = vec && (variant == 2 || variant == 4) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
     default_shape(op, nvec, &G, &NV, &U, half16);
     if (t && t->group_lanes) G = t->group_lanes;
     if (t && t->vecs_per_lane) NV = t->vecs_per_lane;
@@ -395,7 +395,8 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     L->vec = vec;
     L->threads = threads;
     L->chunks = (variant >= 2);
-    L->ring = (variant == 2);
+    L->ring = (variant == 2 || variant == 4);
+    L->lean = (variant == 4);
     const int stages = (t && t->stages) ? t->stages : 2;
     REQUIRE(stages == 2 || stages == 4, SPK_ERR_ARG, "tune.stages must be 2 or 4");
     L->stages = stages;
@@ -412,7 +413,7 @@ extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int3
     spk_status st = resolve(P, op, dt, K, vec, nullptr, &L);
     if (st != SPK_OK) return st;
     const Shape sh = shape_at(L.shape);
-    out->variant = L.chunks ? (L.ring ? 2 : 3) : 1;
+    out->variant = L.chunks ? (L.ring ? (L.lean ? 4 : 2) : 3) : 1;
     out->group_lanes = sh.G;
     out->vecs_per_lane = sh.NV;
     out->unroll = sh.U;
@@ -597,7 +598,7 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
         e = launch_fused_mh(dt, nv, a, (cudaStream_t)stream);
     } else {
         Launch L;
-        L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;
+        L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.lean = false; L.stages = 2;
         e = launch_fused(dt, L, a, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "spk_fusedmm");
@@ -754,6 +755,137 @@ extern "C" spk_status spk_spmm_static(spk_csr S, const float* vals, const float*
     if (st != SPK_OK) return st;
     return spmm_common("spk_spmm_static", S, vals, vals2, dtb, B, ldb, b_scale, K, dtc, C, ldc, accumulate, ws,
                        (size_t)SPK_STATIC_SCRATCH_BYTES, tune, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------------------------------------
+// Dense row-panel tiles on the tensor cores
+// ----------------------------------------------------------------------------
+static int32_t tc_threshold_or_default(int32_t t) { return t == 0 ? 1024 : t; }
+
+extern "C" spk_status spk_tc_plan_size(spk_csr S, int32_t threshold, int32_t chunk_work, size_t* storage_bytes,
+                                       size_t* temp_bytes)
+{
+    REQUIRE(S && storage_bytes && temp_bytes, SPK_ERR_ARG, "spk_tc_plan_size: NULL argument");
+    const int32_t th = tc_threshold_or_default(threshold), W = chunk_work_or_default(chunk_work);
+    REQUIRE(th >= 1 && th <= 128 * 64, SPK_ERR_ARG, "spk_tc_plan_size: threshold %d outside [1, 8192]", th);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_tc_plan_size: chunk_work %d outside [32, 2^20]", W);
+    const TcLayout L = tc_layout(S->M, S->N, S->nnz, th, W);
+    *storage_bytes = L.total;
+    *temp_bytes = L.temp_total;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_plan_build(spk_csr S, int32_t threshold, int32_t chunk_work, void* storage,
+                                        size_t storage_bytes, void* temp, size_t temp_bytes, spk_tcplan* out,
+                                        void* stream)
+{
+    REQUIRE(S && out, SPK_ERR_ARG, "spk_tc_plan_build: NULL argument");
+    *out = nullptr;
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_tc_plan_build: pattern belongs to a transpose plan");
+    const int32_t th = tc_threshold_or_default(threshold), W = chunk_work_or_default(chunk_work);
+    REQUIRE(th >= 1 && th <= 128 * 64, SPK_ERR_ARG, "spk_tc_plan_build: threshold %d outside [1, 8192]", th);
+    REQUIRE(W >= 32 && W <= (1 << 20), SPK_ERR_ARG, "spk_tc_plan_build: chunk_work %d outside [32, 2^20]", W);
+    const TcLayout L = tc_layout(S->M, S->N, S->nnz, th, W);
+    REQUIRE(storage && storage_bytes >= L.total, SPK_ERR_WORKSPACE, "spk_tc_plan_build: storage needs %zu bytes",
+            L.total);
+    REQUIRE(temp && temp_bytes >= L.temp_total, SPK_ERR_WORKSPACE, "spk_tc_plan_build: temp needs %zu bytes",
+            L.temp_total);
+    REQUIRE((reinterpret_cast<uintptr_t>(storage) & 255u) == 0 && (reinterpret_cast<uintptr_t>(temp) & 255u) == 0,
+            SPK_ERR_WORKSPACE, "spk_tc_plan_build: buffers must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* st = reinterpret_cast<char*>(storage);
+    int64_t nt = 0, nd = 0;
+    cudaError_t e = tc_plan_build(S->rowptr, S->colidx, S->M, S->N, S->nnz, th, st, reinterpret_cast<char*>(temp), L,
+                                  &nt, &nd, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_tc_plan_build");
+    spk_tcplan_s* P = new (std::nothrow) spk_tcplan_s();
+    REQUIRE(P, SPK_ERR_ARG, "spk_tc_plan_build: out of host memory");
+    P->M = S->M; P->N = S->N; P->nnz = S->nnz; P->ntiles = nt; P->dense_nnz = nd; P->threshold = th;
+    P->tiles = reinterpret_cast<const int4*>(st + L.tiles);
+    P->ent_slot = reinterpret_cast<const int32_t*>(st + L.ent_slot);
+    P->ent_ij = reinterpret_cast<const int32_t*>(st + L.ent_ij);
+    P->emap = reinterpret_cast<const int32_t*>(st + L.emap);
+    P->status = reinterpret_cast<int32_t*>(st + L.status);
+    spk_csr_s& R = P->Rest;
+    R = spk_csr_s();
+    R.M = S->M; R.N = S->N; R.nnz = S->nnz - nd;
+    R.rowptr = reinterpret_cast<const int32_t*>(st + L.rowptr);
+    R.colidx = reinterpret_cast<const int32_t*>(st + L.colidx);
+    spk_status ss = attach_schedule(&R, W, st + L.sched, L.sl.total, s);
+    if (ss != SPK_OK) { delete P; return ss; }
+    *out = P;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_plan_info(spk_tcplan P, int64_t* tiles, int64_t* dense_nnz, int64_t* rest_nnz)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_tc_plan_info: P is NULL");
+    if (tiles) *tiles = P->ntiles;
+    if (dense_nnz) *dense_nnz = P->dense_nnz;
+    if (rest_nnz) *rest_nnz = P->Rest.nnz;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_plan_arrays(spk_tcplan P, const int32_t** tiles, const int32_t** ent_slot,
+                                         const int32_t** rest_rowptr, const int32_t** rest_colidx,
+                                         const int32_t** rest_emap, int32_t** status)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_tc_plan_arrays: P is NULL");
+    if (tiles) *tiles = reinterpret_cast<const int32_t*>(P->tiles);
+    if (ent_slot) *ent_slot = P->ent_slot;
+    if (rest_rowptr) *rest_rowptr = P->Rest.rowptr;
+    if (rest_colidx) *rest_colidx = P->Rest.colidx;
+    if (rest_emap) *rest_emap = P->emap;
+    if (status) *status = P->status;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_plan_destroy(spk_tcplan P)
+{
+    delete P;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_sddmm_workspace_size(spk_tcplan P, size_t* bytes)
+{
+    REQUIRE(P && bytes, SPK_ERR_ARG, "spk_tc_sddmm_workspace_size: NULL argument");
+    *bytes = align256((size_t)P->Rest.nnz * 4);
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_tc_sddmm(spk_tcplan P, const float* vals, spk_dtype dt, const void* A, int64_t lda,
+                                   const void* B, int64_t ldb, int32_t K, float* out, void* workspace,
+                                   size_t ws_bytes, const spk_tune* tune, void* stream)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_tc_sddmm: P is NULL");
+    REQUIRE(dt == SPK_BF16, SPK_ERR_DTYPE, "spk_tc_sddmm: the tensor-core tiles take BF16 operands");
+    REQUIRE(K >= 16 && K <= 256 && K % 16 == 0, SPK_ERR_SHAPE, "spk_tc_sddmm: K must be a multiple of 16 in [16, 256]");
+    REQUIRE(lda >= K && ldb >= K, SPK_ERR_SHAPE, "spk_tc_sddmm: leading dimensions must be >= K");
+    REQUIRE(P->nnz == 0 || (A && B && out), SPK_ERR_ARG, "spk_tc_sddmm: NULL operand");
+    REQUIRE(aligned16(A) && aligned16(B) && (lda * 2) % 16 == 0 && (ldb * 2) % 16 == 0, SPK_ERR_SHAPE,
+            "spk_tc_sddmm: A and B must be 16-byte aligned with 16-byte row strides");
+    const size_t need = align256((size_t)P->Rest.nnz * 4);
+    REQUIRE(P->Rest.nnz == 0 || (workspace && ws_bytes >= need), SPK_ERR_WORKSPACE,
+            "spk_tc_sddmm: workspace has %zu bytes, needs %zu", workspace ? ws_bytes : (size_t)0, need);
+    REQUIRE(aligned16(workspace), SPK_ERR_WORKSPACE, "spk_tc_sddmm: workspace must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the remainder on the gather kernels (unit values), then scaled into place
+    if (P->Rest.nnz > 0) {
+        float* rest = reinterpret_cast<float*>(workspace);
+        spk_status st = spk_sddmm(&P->Rest, nullptr, nullptr, dt, A, lda, nullptr, dt, B, ldb, nullptr, K, rest, tune,
+                                  stream);
+        if (st != SPK_OK) return st;
+        cudaError_t e = launch_scatter_scale(P->emap, vals, rest, P->Rest.nnz, out, s);
+        if (e != cudaSuccess) return cuda_fail(e, "spk_tc_sddmm remainder");
+    }
+    TcArgs a;
+    a.M = P->M; a.N = P->N; a.K = K;
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
+    a.tiles = P->tiles; a.ent_slot = P->ent_slot; a.ent_ij = P->ent_ij;
+    a.vals = vals; a.out = out; a.status = P->status;
+    cudaError_t e = launch_tc_sddmm(a, P->ntiles, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_tc_sddmm tiles");
+    return SPK_OK;
 }
 
 // ----------------------------------------------------------------------------

@@ -362,6 +362,7 @@ struct Launch {
     int threads;
     bool chunks;       // balanced schedule
     bool ring;         // stage gathered rows in a shared-memory ring where the path has one
+    bool lean;         // the ring's lean form (tiles unrolled; SpMM, one vector per lane)
     int stages;        // batch slots of the ring (2 or 4)
 };
 
@@ -435,6 +436,34 @@ cudaError_t permute_pattern(const int32_t* rowptr, const int32_t* colidx, int64_
 cudaError_t permute_rows(const void* X, int64_t ldx_b, int64_t M, int64_t bytes, const int32_t* perm, int scatter,
                          void* Y, int64_t ldy_b, cudaStream_t s);
 cudaError_t permute_values(const float* x, const int32_t* map, int64_t n, int scatter, float* y, cudaStream_t s);
+// Dense row-panel tiles on the tensor cores (tc.cu)
+struct TcArgs {
+    int64_t M, N;
+    int32_t K;
+    const void* A; int64_t lda;      // BF16, M x K
+    const void* B; int64_t ldb;      // BF16, N x K
+    const int4* tiles;               // {panel, column tile, first entry, entries} per dense tile
+    const int32_t* ent_slot;         // slot in S of each dense-tile entry
+    const int32_t* ent_ij;           // (row in panel) << 16 | (column in tile)
+    const float* vals;               // NULL = ones
+    float* out;
+    int32_t* status;                 // set to 1 if a tensor-core wait ran out
+};
+size_t tc_sddmm_smem(int K);
+cudaError_t launch_tc_sddmm(const TcArgs& a, int64_t ntiles, cudaStream_t s);
+struct TcLayout {
+    size_t tiles, ent_slot, ent_ij, rowptr, colidx, emap, status, sched, total;     // storage
+    size_t rows, key, k0, k1, v0, v1, key2, order, kp, start, runid, runbeg, dense, entries, tileix, entoff, isdense,
+        cnt, hist, scan, temp_total;
+    int64_t max_tiles;
+    SchedLayout sl;
+};
+TcLayout tc_layout(int64_t M, int64_t N, int64_t nnz, int32_t threshold, int32_t W);
+cudaError_t tc_plan_build(const int32_t* rowptr, const int32_t* colidx, int64_t M, int64_t N, int64_t nnz,
+                          int32_t threshold, char* storage, char* temp, const TcLayout& L, int64_t* ntiles,
+                          int64_t* dense_nnz, cudaStream_t s);
+cudaError_t launch_scatter_scale(const int32_t* map, const float* vals, const float* x, int64_t n, float* out,
+                                 cudaStream_t s);
 // COO -> CSR (coo.cu)
 size_t coo_temp_bytes(int64_t M, int64_t N, int64_t nnz);
 cudaError_t coo_to_csr(int64_t M, int64_t N, int64_t nnz, const int32_t* rows, const int32_t* cols, const float* vals,
@@ -465,6 +494,17 @@ struct spk_csr_s {
     const int32_t* head_s0;
     const int32_t* slot_np;
     int32_t* cnt;
+};
+
+struct spk_tcplan_s {
+    spk_csr_s Rest;           // entries outside dense tiles (with their schedule); rowptr/colidx in storage
+    const int4* tiles;
+    const int32_t* ent_slot;
+    const int32_t* ent_ij;
+    const int32_t* emap;      // slot in S of each remainder entry
+    int32_t* status;
+    int64_t M, N, nnz, ntiles, dense_nnz;
+    int32_t threshold;
 };
 
 struct spk_tplan_s {

@@ -8,7 +8,7 @@ import ctypes
 import torch
 
 from .binding import SPK_BF16, SPK_E4M3, SPK_F16, SPK_F32, Tune, check, lib
-from .sparse import CSR, TransposePlan, _stream
+from .sparse import CSR, TensorCorePlan, TransposePlan, _stream
 
 _DT = {torch.float32: SPK_F32, torch.bfloat16: SPK_BF16, torch.float16: SPK_F16,
        torch.float8_e4m3fn: SPK_E4M3, torch.uint8: SPK_E4M3}
@@ -237,3 +237,26 @@ def quantize_e4m3_rows(X: torch.Tensor):
 
 __all__ = ["sddmm", "spmm", "spmm_t", "fusedmm", "fused_weights", "fused_rowdot", "fused_score_grad", "cast",
            "quantize_e4m3_rows"]
+
+
+def tc_sddmm(P: TensorCorePlan, A: torch.Tensor, B: torch.Tensor, vals=None, *, out: torch.Tensor | None = None,
+             tune=None, use_default_vals: bool = True) -> torch.Tensor:
+    """SDDMM (Eq. 1) with the plan's dense tiles on the tensor cores and the
+    remaining entries on the gather kernels.  A, B BF16."""
+    S = P.S
+    if vals is None and use_default_vals:
+        vals = S.vals
+    dta, lda = _dense(A, "A", S.device)
+    dtb, ldb = _dense(B, "B", S.device)
+    if A.size(0) != S.M or B.size(0) != S.N or A.size(1) != B.size(1):
+        raise ValueError(f"shapes: S {S.M}x{S.N}, A {tuple(A.shape)}, B {tuple(B.shape)}")
+    if dta != dtb:
+        raise TypeError("A and B must have the same dtype")
+    if out is None:
+        out = torch.empty(S.nnz, dtype=torch.float32, device=S.device)
+    vals = _vals(vals, S, "vals")
+    ws = P.workspace()
+    check(lib().spk_tc_sddmm(P.handle, _ptr(vals), dta, A.data_ptr(), lda, B.data_ptr(), ldb, A.size(1),
+                             out.data_ptr(), _ptr(ws), 0 if ws is None else ws.numel(), _tune(tune),
+                             _stream(S.device)), "spk_tc_sddmm")
+    return out

@@ -330,3 +330,67 @@ class Reordering:
         """Per-entry results on S' back to the slot order of S."""
         return self._vals(xp, 1)
 
+
+class TensorCorePlan:
+    """Dense 128 x 64 tiles of a pattern for the tensor cores, and the rest
+    (spk_tc_plan_build): tiles holding at least ``threshold`` entries run as
+    dense contractions, every other entry on the gather kernels."""
+
+    def __init__(self, S: CSR, threshold: int = 1024, *, chunk_work: int = DEFAULT_CHUNK_WORK):
+        self.S = S
+        self.M, self.N, self.nnz = S.M, S.N, S.nnz
+        st, tmp = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().spk_tc_plan_size(S.handle, int(threshold), int(chunk_work), ctypes.byref(st), ctypes.byref(tmp)),
+              "spk_tc_plan_size")
+        self._storage = _buffer(st.value, S.device)
+        temp = _buffer(tmp.value, S.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(S.device):
+            check(lib().spk_tc_plan_build(S.handle, int(threshold), int(chunk_work), self._storage.data_ptr(),
+                                          self._storage.numel(), temp.data_ptr(), temp.numel(), ctypes.byref(self._h),
+                                          _stream(S.device)), "spk_tc_plan_build")
+        del temp
+        self._ws = None
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def info(self) -> dict:
+        t, d, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().spk_tc_plan_info(self._h, ctypes.byref(t), ctypes.byref(d), ctypes.byref(r)), "spk_tc_plan_info")
+        return {"tiles": t.value, "dense_nnz": d.value, "rest_nnz": r.value}
+
+    def arrays(self) -> dict:
+        """Device views: tiles (T x 4), dense-entry slots, the remainder's
+        rowptr / colidx / slots, and the status word."""
+        ptrs = [ctypes.c_void_p() for _ in range(6)]
+        check(lib().spk_tc_plan_arrays(self._h, *[ctypes.byref(p) for p in ptrs]), "spk_tc_plan_arrays")
+        base = self._storage.data_ptr()
+        inf = self.info()
+
+        def view(ptr, n):
+            off = ptr.value - base
+            return self._storage[off:off + 4 * n].view(torch.int32)
+
+        return {"tiles": view(ptrs[0], 4 * inf["tiles"]).view(-1, 4), "ent_slot": view(ptrs[1], inf["dense_nnz"]),
+                "rest_rowptr": view(ptrs[2], self.M + 1), "rest_colidx": view(ptrs[3], inf["rest_nnz"]),
+                "rest_emap": view(ptrs[4], inf["rest_nnz"]), "status": view(ptrs[5], 1)}
+
+    def workspace(self) -> torch.Tensor | None:
+        n = ctypes.c_size_t()
+        check(lib().spk_tc_sddmm_workspace_size(self._h, ctypes.byref(n)), "spk_tc_sddmm_workspace_size")
+        if n.value == 0:
+            return None
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = _buffer(n.value, self.S.device)
+        return self._ws
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().spk_tc_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None

@@ -230,6 +230,33 @@ def tiny(seed: int = 0, M: int = 4096, N: int = 4096, deg: int = 16, K: int = 32
                    uniform((N, K), -1.0, 1.0, seed, _B))
 
 
+def dense_blocks(M: int, N: int, blocks: int, density: float, background_deg: int, seed: int,
+                 block_shape=(128, 64), aligned: bool = True, sub: int = 0):
+    """A sparse background of exactly ``background_deg`` distinct uniform
+    columns per row, plus ``blocks`` rectangles of ``block_shape`` whose cells
+    are each present with probability ``density`` (at positions that are
+    multiples of the block shape when ``aligned``, anywhere otherwise).
+    Duplicates are removed.  Returns (rowptr, colidx)."""
+    g = rng(seed, _PATTERN, sub)
+    rp, ci = er_exact_degree(M, N, background_deg, seed, sub) if background_deg else (np.zeros(M + 1, np.int32),
+                                                                                       np.zeros(0, np.int32))
+    rows = [np.repeat(np.arange(M), np.diff(rp))]
+    cols = [ci.astype(np.int64)]
+    bh, bw = block_shape
+    for _ in range(blocks):
+        if aligned:
+            r0 = int(g.integers(0, max(1, M // bh))) * bh
+            c0 = int(g.integers(0, max(1, N // bw))) * bw
+        else:
+            r0 = int(g.integers(0, max(1, M - bh)))
+            c0 = int(g.integers(0, max(1, N - bw)))
+        cell = g.random((min(bh, M - r0), min(bw, N - c0))) < density
+        rr, cc = np.nonzero(cell)
+        rows.append(rr + r0)
+        cols.append(cc + c0)
+    return csr_from_coo(np.concatenate(rows), np.concatenate(cols), M, N)
+
+
 def rmat_problem(scale: int = 20, edge_factor: int = 16, K: int = 64, seed: int = 0,
                  name: str = "rmat20") -> Problem:
     rp, ci = rmat(scale, edge_factor, seed)
