@@ -475,6 +475,50 @@ def aux_measurements(spk, S, P, A32, A, B, dt, elt, flush, stream, args):
 
 
 
+def other_workloads(spk, dev, flush, stream, pk, args):
+    """SDDMM and SpMM of the other power-law configurations, timed like the
+    line's step (CUDA events on the launching stream, L2 flushed before each
+    launch): rec (2M x 500K, 50M nnz, K = 128) with FP32 and BF16 factors, and
+    gnn (R-MAT scale 22, K = 64) with BF16 H as both factors."""
+    import torch
+    out = {}
+    for name, dtypes in (("rec", ("f32", "bf16")), ("gnn", ("bf16",))):
+        t0 = time.perf_counter()
+        P, desc = load_workload(name)
+        gen_s = time.perf_counter() - t0
+        vals = None if P.vals is None else torch.from_numpy(P.vals).to(dev)
+        S = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), vals, device=dev, chunk_work=args.chunk_work)
+        A32 = torch.from_numpy(P.A).to(dev)
+        B32 = A32 if P.B is P.A else torch.from_numpy(P.B).to(dev)
+        res = {"workload": desc, "M": P.M, "N": P.N, "K": P.K, "nnz": P.nnz, "generation_s": round(gen_s, 1)}
+        o = torch.empty(P.nnz, dtype=torch.float32, device=dev)
+        C = torch.empty((P.M, P.K), dtype=torch.float32, device=dev)
+        for dt in dtypes:
+            if dt == "f32":
+                A, B, elt = A32, B32, 4
+            else:
+                A = spk.cast(A32, torch.bfloat16)
+                B = A if P.B is P.A else spk.cast(B32, torch.bfloat16)
+                elt = 2
+            sd = event_ms(lambda: spk.sddmm(S, A, B, out=o), stream, flush, reps=10)
+            sp = event_ms(lambda: spk.spmm(S, B, out=C), stream, flush, reps=10)
+            ab = algorithmic_bytes(P, elt)
+            res[dt] = {"sddmm_ms": sd, "spmm_ms": sp,
+                       "sddmm_gflops": 2.0 * P.nnz * P.K / (sd / 1e3) / 1e9,
+                       "spmm_gflops": 2.0 * P.nnz * P.K / (sp / 1e3) / 1e9,
+                       "sddmm_algo_gbs": ab["sddmm"] / (sd / 1e3) / 1e9,
+                       "spmm_algo_gbs": ab["spmm"] / (sp / 1e3) / 1e9,
+                       "sddmm_frac": ab["sddmm"] / (sd / 1e3) / 1e9 / pk["hbm_gbs"],
+                       "spmm_frac": ab["spmm"] / (sp / 1e3) / 1e9 / pk["hbm_gbs"]}
+            del A, B
+        out[name] = res
+        del S, A32, B32, o, C, vals, P
+        torch.cuda.empty_cache()
+    out["note"] = ("median of 10 CUDA-event timings per kernel, L2 flushed before each; algorithmic bytes as for "
+                   "the line's roofline (factors once, indices, values, outputs); frac of the measured copy peak")
+    return out
+
+
 def main(args):
     if args.impl == "reference":
         return reference_arm(args)
@@ -703,6 +747,11 @@ def main(args):
     if aux is not None:
         line["aux"] = aux
     line["clocks"] = clocks
+    if world == 1 and not args.no_extra and args.workload == "rmat20":
+        try:
+            line["other_workloads"] = other_workloads(spk, dev, flush, stream, pk, args)
+        except Exception as exc:                    # keep the line if this extra measurement fails
+            line["other_workloads"] = {"error": str(exc)[:200]}
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -925,6 +974,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-aux", action="store_true", help="skip the setup / SpMM^T / conversion measurements")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-factor timing of the FP32 line")
+    ap.add_argument("--no-extra", action="store_true", help="skip the rec and gnn kernel timings")
     a = ap.parse_args()
     a.warmup_requested = a.warmup
     if a.warmup < 3:                # the timing rules ask for at least 3 warm-up steps; the line says so

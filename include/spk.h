@@ -70,9 +70,7 @@ typedef struct spk_tune {
     int32_t variant;        /* 0 default, 1 row-split (one lane group per row),
                                2 balanced chunks (merge-path schedule, needs spk_schedule_build),
                                  gathered rows staged in shared memory where the path supports it,
-                               3 balanced chunks, gathered rows held in registers,
-                               4 as 2, SpMM in the ring's lean form where it applies
-                                 (one vector per lane, K covered by whole blocks) */
+                               3 balanced chunks, gathered rows held in registers */
     int32_t group_lanes;    /* lanes that share one row of the dense factor: 4, 8, 16, 32 */
     int32_t vecs_per_lane;  /* 16-byte vectors each lane holds per K block: 1, 2, 4 */
     int32_t unroll;         /* nonzeros in flight per group: 4, 8                  */
@@ -90,6 +88,9 @@ const char* spk_status_string(spk_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char* spk_last_error(void);
 int32_t spk_version(void);
+/* The (group_lanes, vecs_per_lane, unroll) shapes compiled into the library:
+ * writes min(count, capacity) triples to out (may be NULL), returns count. */
+int32_t spk_shapes(int32_t* out, int32_t capacity);
 /* The tune a default call would use for this op (0 SDDMM, 1 SpMM, 2 SpMM^T),
  * dtype of the gathered operand, and K.  Fills *out. */
 spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int32_t K, spk_tune* out);
@@ -213,6 +214,18 @@ spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
                     spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
                     spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate,
                     void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
+
+/* SpMM with one value array per head: heads equal slices of K, head h
+ * (columns h*K/heads .. (h+1)*K/heads - 1) multiplying by its own values
+ * vals[h * hstride + e] (e in colidx order; NULL = ones):
+ *   C[i, head h] (+)= sum_{e=(i,j)} vals[h * hstride + e] * B[j, head h]
+ * It is the product that the backward of a multi-head SDDMM -> SpMM cascade
+ * needs (one SpMM per head otherwise, each reading the whole pattern).  B is
+ * F32, BF16 or F16 (16-byte aligned rows, K/heads a whole number of 16-byte
+ * vectors); C is FP32.  Workspace as spk_spmm. */
+spk_status spk_spmm_mh(spk_csr S, const float* vals, int64_t hstride, int32_t heads, spk_dtype dtb, const void* B,
+                       int64_t ldb, int32_t K, float* C, int64_t ldc, int32_t accumulate, void* workspace,
+                       size_t ws_bytes, void* stream);
 
 /* Scratch held by the library for spk_spmm_static, in bytes (4 MiB): a
  * file-scope device array that every GPU loading the library keeps until the
@@ -354,6 +367,15 @@ spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* vals2,
                       spk_dtype dty, const void* Y, int64_t ldy, const float* y_scale, int32_t K,
                       spk_dtype dtx, void* X, int64_t ldx, int32_t accumulate,
                       void* workspace, size_t ws_bytes, const spk_tune* tune, void* stream);
+
+/* X (N x K, FP32) (+)= S^T Y with one value array per head (as spk_spmm_mh):
+ * X[j, head h] = sum_{e=(i,j)} vals[h * hstride + e] * Y[i, head h].  The
+ * arrays go to CSC slot order in the workspace (size from
+ * spk_spmm_t_mh_workspace_size, 256-byte aligned) first. */
+spk_status spk_spmm_t_mh_workspace_size(spk_tplan P, int32_t K, int32_t heads, size_t* bytes);
+spk_status spk_spmm_t_mh(spk_tplan P, const float* vals, int64_t hstride, int32_t heads, spk_dtype dty, const void* Y,
+                         int64_t ldy, int32_t K, float* X, int64_t ldx, int32_t accumulate, void* workspace,
+                         size_t ws_bytes, void* stream);
 
 /* ----------------------------------------------------------- precision -- */
 /* Round-to-nearest-even casts of n FP32 values to BF16 or F16. */

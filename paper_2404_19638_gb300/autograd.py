@@ -130,8 +130,10 @@ class FusedMMFunction(torch.autograd.Function):
       holding c, w)
     Steps: one SDDMM per head for dw, the row term and score gradient
     kernels (c folds in the sparse values, so every SpMM takes one value
-    array), then SpMM / SpMM^T per head accumulating in FP32.  The sparse
-    values are not differentiated.
+    array per head), then dA = one multi-head SpMM (c per head) and
+    dB = two multi-head SpMM^T (c with A, then w with dY added), each one
+    pass over the pattern for all heads, in FP32.  The sparse values are not
+    differentiated.
     """
 
     @staticmethod
@@ -160,19 +162,12 @@ class FusedMMFunction(torch.autograd.Function):
         c = ops.fused_score_grad(S, w, dw, R, heads, softmax, scale, v)
         dA = dB = None
         if ctx.needs_input_grad[2]:
-            dA = torch.empty((S.M, K), dtype=torch.float32, device=S.device)
-            for h in range(heads):
-                c0 = h * Kh
-                ops.spmm(S, B[:, c0:c0 + Kh], c[h], out=dA[:, c0:c0 + Kh], use_default_vals=False)
+            dA = ops.spmm_mh(S, B, c, heads)
             if A.dtype != torch.float32:
                 dA = ops.cast(dA, A.dtype)
         if ctx.needs_input_grad[3]:
-            dB = torch.empty((S.N, K), dtype=torch.float32, device=S.device)
-            for h in range(heads):
-                c0 = h * Kh
-                ops.spmm_t(S, A[:, c0:c0 + Kh], c[h], out=dB[:, c0:c0 + Kh], use_default_vals=False)
-                ops.spmm_t(S, dY[:, c0:c0 + Kh], w[h], out=dB[:, c0:c0 + Kh], accumulate=True,
-                           use_default_vals=False)
+            dB = ops.spmm_t_mh(S, A, c, heads)
+            ops.spmm_t_mh(S, dY, w, heads, out=dB, accumulate=True)
             if B.dtype != torch.float32:
                 dB = ops.cast(dB, B.dtype)
         return None, None, dA, dB, None, None, None

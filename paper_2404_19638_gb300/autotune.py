@@ -28,8 +28,6 @@ from .binding import SpkError
 from .sparse import CSR
 
 _VEC = {torch.float32: 4, torch.bfloat16: 8, torch.float16: 8, torch.float8_e4m3fn: 16, torch.uint8: 16}
-_COMPILED = {(4, 1, 4), (8, 1, 8), (16, 1, 8), (32, 1, 8), (8, 2, 8), (16, 2, 8), (32, 2, 4), (4, 2, 4), (32, 4, 4),
-             (16, 1, 4), (8, 2, 4), (8, 1, 4), (8, 4, 4)}
 
 
 def pattern_signature(rowptr: np.ndarray, M: int, N: int) -> str:
@@ -47,8 +45,9 @@ def candidate_shapes(K: int, dtype) -> list[tuple[int, int, int]]:
     without more than half the lanes idle."""
     vec = _VEC.get(dtype, 4)
     nvec = max(1, K // vec) if K % vec == 0 else K
+    from .binding import compiled_shapes
     out = []
-    for (G, NV, U) in sorted(_COMPILED):
+    for (G, NV, U) in sorted(compiled_shapes()):
         cover = G * NV
         if cover >= nvec and cover <= max(4, 2 * nvec):
             out.append((G, NV, U))

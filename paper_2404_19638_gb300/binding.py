@@ -53,6 +53,7 @@ _PROTOS = {
     "spk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "spk_last_error": (ctypes.c_char_p, []),
     "spk_version": (_i32, []),
+    "spk_shapes": (_i32, [_vp, _i32]),
     "spk_tune_default": (ctypes.c_int, [_vp, _i32, ctypes.c_int, _i32, _P(Tune)]),
     "spk_csr_create": (ctypes.c_int, [_P(_vp), _i64, _i64, _i64, _vp, _vp]),
     "spk_csr_destroy": (ctypes.c_int, [_vp]),
@@ -74,6 +75,11 @@ _PROTOS = {
                                  _vp, _P(Tune), _vp]),
     "spk_spmm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _i64, _vp, _i32, ctypes.c_int, _vp, _i64, _i32,
                                 _vp, _sz, _P(Tune), _vp]),
+    "spk_spmm_mh": (ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _sz,
+                                   _vp]),
+    "spk_spmm_t_mh_workspace_size": (ctypes.c_int, [_vp, _i32, _i32, _P(_sz)]),
+    "spk_spmm_t_mh": (ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _sz,
+                                     _vp]),
     "spk_spmm_static": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _i64, _vp, _i32, ctypes.c_int, _vp, _i64,
                                        _i32, _P(Tune), _vp]),
     "spk_fusedmm_workspace_size": (ctypes.c_int, [_vp, _i32, _i32, _P(_sz)]),
@@ -138,3 +144,11 @@ def check(status: int, where: str) -> None:
     if status != 0:
         msg = lib().spk_last_error()
         raise SpkError(status, where, msg.decode() if msg else "")
+
+
+def compiled_shapes() -> list[tuple[int, int, int]]:
+    """(group_lanes, vecs_per_lane, unroll) shapes compiled into libspk."""
+    n = lib().spk_shapes(None, 0)
+    buf = (ctypes.c_int32 * (3 * n))()
+    lib().spk_shapes(buf, n)
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]

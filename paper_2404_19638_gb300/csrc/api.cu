@@ -376,12 +376,12 @@ static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16
 static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, const spk_tune* t, Launch* L)
 {
     const int variant = (t && t->variant) ? t->variant : (S->has_sched ? 2 : 1);
-    REQUIRE(variant >= 1 && variant <= 4, SPK_ERR_ARG, "tune.variant %d is not 0, 1, 2, 3 or 4", variant);
+    REQUIRE(variant >= 1 && variant <= 3, SPK_ERR_ARG, "tune.variant %d is not 0, 1, 2 or 3", variant);
     REQUIRE(variant == 1 || S->has_sched, SPK_ERR_STATE, "balanced variant needs spk_schedule_build first");
     const int vecn = vec ? vec_elems(dtb) : 1;
     const int nvec = K / vecn;
     int G, NV, U;
-    const bool half16 = vec && (variant == 2 || variant == 4) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
+    const bool half16 = vec && (variant == 2) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
     default_shape(op, nvec, &G, &NV, &U, half16);
     if (t && t->group_lanes) G = t->group_lanes;
     if (t && t->vecs_per_lane) NV = t->vecs_per_lane;
@@ -395,12 +395,23 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     L->vec = vec;
     L->threads = threads;
     L->chunks = (variant >= 2);
-    L->ring = (variant == 2 || variant == 4);
-    L->lean = (variant == 4);
+    L->ring = (variant == 2);
     const int stages = (t && t->stages) ? t->stages : 2;
     REQUIRE(stages == 2 || stages == 4, SPK_ERR_ARG, "tune.stages must be 2 or 4");
     L->stages = stages;
     return SPK_OK;
+}
+
+extern "C" int32_t spk_shapes(int32_t* out, int32_t capacity)
+{
+    if (out)
+        for (int i = 0; i < kNumShapes && i < capacity; ++i) {
+            const Shape sh = shape_at(i);
+            out[3 * i] = sh.G;
+            out[3 * i + 1] = sh.NV;
+            out[3 * i + 2] = sh.U;
+        }
+    return kNumShapes;
 }
 
 extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int32_t K, spk_tune* out)
@@ -413,7 +424,7 @@ extern "C" spk_status spk_tune_default(spk_csr S, int32_t op, spk_dtype dt, int3
     spk_status st = resolve(P, op, dt, K, vec, nullptr, &L);
     if (st != SPK_OK) return st;
     const Shape sh = shape_at(L.shape);
-    out->variant = L.chunks ? (L.ring ? (L.lean ? 4 : 2) : 3) : 1;
+    out->variant = L.chunks ? (L.ring ? 2 : 3) : 1;
     out->group_lanes = sh.G;
     out->vecs_per_lane = sh.NV;
     out->unroll = sh.U;
@@ -473,7 +484,7 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
                               spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale, int32_t K,
                               spk_dtype dtc, void* C, int64_t ldc, int32_t accumulate, void* ws, size_t ws_bytes,
                               const spk_tune* tune, cudaStream_t stream, bool vals_in_slot_order = false,
-                              bool check_only = false)
+                              bool check_only = false, int32_t heads = 1, int64_t hstride = 0)
 {
     REQUIRE(valid_dt(dtb), SPK_ERR_DTYPE, "%s: unknown input dtype", name);
     REQUIRE(dtc == SPK_F32 || dtc == SPK_BF16 || dtc == SPK_F16, SPK_ERR_DTYPE,
@@ -489,7 +500,24 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
     const bool vec = (K % vecn) == 0 && aligned16(B) && aligned16(C) && (ldb * dt_bytes(dtb)) % 16 == 0 &&
                      (ldc * dt_bytes(dtc)) % 16 == 0;
     Launch L;
-    spk_status st = resolve(S, OP_SPMM, dtb, K, vec, tune, &L);
+    spk_status st;
+    if (heads > 1) {
+        // one head per lane: one 16-byte vector per lane (NV = 1), G lanes per K block
+        REQUIRE(vec, SPK_ERR_UNSUPPORTED, "%s: several heads need 16-byte aligned rows and K a multiple of %d", name,
+                vecn);
+        const int nv = K / vecn;
+        REQUIRE(nv % heads == 0, SPK_ERR_UNSUPPORTED, "%s: %d vectors per row do not split into %d heads", name, nv,
+                heads);
+        const int G = nv <= 4 ? 4 : (nv <= 8 ? 8 : (nv <= 16 ? 16 : 32));
+        spk_tune t{};
+        t.variant = S->has_sched ? 3 : 1;
+        t.group_lanes = G;
+        t.vecs_per_lane = 1;
+        t.unroll = G == 4 ? 4 : 8;
+        st = resolve(S, OP_SPMM, dtb, K, vec, &t, &L);
+    } else {
+        st = resolve(S, OP_SPMM, dtb, K, vec, tune, &L);
+    }
     if (st != SPK_OK) return st;
     if (L.chunks && S->npieces > 0) {
         const size_t need = (size_t)S->npieces * (size_t)K * 4;
@@ -503,7 +531,9 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
     a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
     a.vperm = vals_in_slot_order ? nullptr : S->vperm;
     a.vals = vals; a.vals2 = vals2;
-    a.vals_staged = (vals && !vals2 && !a.vperm && aligned16(vals)) ? 1 : 0;
+    a.vals_staged = (vals && !vals2 && !a.vperm && aligned16(vals) && (heads == 1 || hstride % 4 == 0)) ? 1 : 0;
+    a.heads = heads;
+    a.hstride = hstride;
     a.B = B; a.ldb = ldb; a.b_scale = b_scale;
     a.C = C; a.ldc = ldc; a.dtc = dtc; a.accumulate = accumulate;
     a.bnd = L.chunks ? S->bnd : nullptr;
@@ -523,6 +553,21 @@ extern "C" spk_status spk_spmm(spk_csr S, const float* vals, const float* vals2,
     REQUIRE(S, SPK_ERR_ARG, "spk_spmm: S is NULL");
     return spmm_common("spk_spmm", S, vals, vals2, dtb, B, ldb, b_scale, K, dtc, C, ldc, accumulate, workspace,
                        ws_bytes, tune, (cudaStream_t)stream);
+}
+
+// Several heads (equal slices of K), each with its own value array.
+extern "C" spk_status spk_spmm_mh(spk_csr S, const float* vals, int64_t hstride, int32_t heads, spk_dtype dtb,
+                                  const void* B, int64_t ldb, int32_t K, float* C, int64_t ldc, int32_t accumulate,
+                                  void* workspace, size_t ws_bytes, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_spmm_mh: S is NULL");
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_spmm_mh: pattern belongs to a transpose plan");
+    REQUIRE(heads >= 1 && K >= 1 && K % heads == 0, SPK_ERR_SHAPE, "spk_spmm_mh: K (%d) must be a multiple of heads (%d)",
+            K, heads);
+    REQUIRE(dtb == SPK_F32 || dtb == SPK_BF16 || dtb == SPK_F16, SPK_ERR_DTYPE, "spk_spmm_mh: B must be F32, BF16 or F16");
+    REQUIRE(heads == 1 || !vals || hstride >= S->nnz, SPK_ERR_ARG, "spk_spmm_mh: hstride below nnz");
+    return spmm_common("spk_spmm_mh", S, vals, nullptr, dtb, B, ldb, nullptr, K, SPK_F32, C, ldc, accumulate, workspace,
+                       ws_bytes, nullptr, (cudaStream_t)stream, false, false, heads, hstride);
 }
 
 // ----------------------------------------------------------------------------
@@ -598,7 +643,7 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
         e = launch_fused_mh(dt, nv, a, (cudaStream_t)stream);
     } else {
         Launch L;
-        L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.lean = false; L.stages = 2;
+        L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;
         e = launch_fused(dt, L, a, (cudaStream_t)stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "spk_fusedmm");
@@ -994,6 +1039,52 @@ extern "C" spk_status spk_spmm_t(spk_tplan P, const float* vals, const float* va
     }
     return spmm_common("spk_spmm_t", &P->St, vt, nullptr, dty, Y, ldy, y_scale, K, dtx, X, ldx, accumulate,
                        w ? w + vb : nullptr, w ? ws_bytes - vb : 0, tune, (cudaStream_t)stream, true);
+}
+
+// S^T Y with one value array per head: the arrays go to CSC slot order in the
+// workspace (heads x round_up(nnz, 4) floats), then the multi-head SpMM on S^T.
+static size_t spmm_t_mh_vals_bytes(const spk_tplan_s* P, int32_t heads)
+{
+    return (((size_t)P->St.nnz + 3) / 4 * 4 * (size_t)heads * 4 + 255) & ~(size_t)255;
+}
+
+extern "C" spk_status spk_spmm_t_mh_workspace_size(spk_tplan P, int32_t K, int32_t heads, size_t* bytes)
+{
+    REQUIRE(P && bytes && K >= 1 && heads >= 1, SPK_ERR_ARG, "spk_spmm_t_mh_workspace_size: bad argument");
+    *bytes = spmm_t_mh_vals_bytes(P, heads) + (size_t)P->St.npieces * (size_t)K * 4;
+    return SPK_OK;
+}
+
+extern "C" spk_status spk_spmm_t_mh(spk_tplan P, const float* vals, int64_t hstride, int32_t heads, spk_dtype dty,
+                                    const void* Y, int64_t ldy, int32_t K, float* X, int64_t ldx, int32_t accumulate,
+                                    void* workspace, size_t ws_bytes, void* stream)
+{
+    REQUIRE(P, SPK_ERR_ARG, "spk_spmm_t_mh: P is NULL");
+    REQUIRE(heads >= 1 && K >= 1 && K % heads == 0, SPK_ERR_SHAPE,
+            "spk_spmm_t_mh: K (%d) must be a multiple of heads (%d)", K, heads);
+    REQUIRE(dty == SPK_F32 || dty == SPK_BF16 || dty == SPK_F16, SPK_ERR_DTYPE, "spk_spmm_t_mh: Y must be F32, BF16 or F16");
+    REQUIRE(heads == 1 || !vals || hstride >= P->St.nnz, SPK_ERR_ARG, "spk_spmm_t_mh: hstride below nnz");
+    const size_t vb = spmm_t_mh_vals_bytes(P, heads);
+    const size_t need = vb + (size_t)P->St.npieces * (size_t)K * 4;
+    REQUIRE(workspace && ws_bytes >= need, SPK_ERR_WORKSPACE, "spk_spmm_t_mh: workspace has %zu bytes, needs %zu",
+            workspace ? ws_bytes : (size_t)0, need);
+    REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255u) == 0, SPK_ERR_WORKSPACE,
+            "spk_spmm_t_mh: workspace must be 256-byte aligned");
+    char* w = reinterpret_cast<char*>(workspace);
+    const int64_t ws_stride = (P->St.nnz + 3) / 4 * 4;
+    const float* vt = vals ? reinterpret_cast<const float*>(w) : nullptr;
+    spk_status st = spmm_common("spk_spmm_t_mh", &P->St, vt, nullptr, dty, Y, ldy, nullptr, K, SPK_F32, X, ldx,
+                                accumulate, w + vb, ws_bytes - vb, nullptr, (cudaStream_t)stream, true, true, heads,
+                                ws_stride);
+    if (st != SPK_OK) return st;
+    if (vals && P->St.nnz > 0)
+        for (int h = 0; h < heads; ++h) {
+            cudaError_t e = launch_permute_vals(P->perm, vals + (int64_t)h * hstride, nullptr, P->St.nnz,
+                                                reinterpret_cast<float*>(w) + (int64_t)h * ws_stride, (cudaStream_t)stream);
+            if (e != cudaSuccess) return cuda_fail(e, "spk_spmm_t_mh value permutation");
+        }
+    return spmm_common("spk_spmm_t_mh", &P->St, vt, nullptr, dty, Y, ldy, nullptr, K, SPK_F32, X, ldx, accumulate,
+                       w + vb, ws_bytes - vb, nullptr, (cudaStream_t)stream, true, false, heads, ws_stride);
 }
 
 // ----------------------------------------------------------------------------

@@ -289,6 +289,8 @@ struct SpmmArgs {
     int64_t M, N, nnz;
     int32_t K;
     int32_t vals_staged;      // vals is 16-byte aligned and used alone: stream it with the indices
+    int32_t heads = 1;        // value arrays, one per equal slice of K (1: one array for all columns)
+    int64_t hstride = 0;      // elements from one head's value array to the next
     const int32_t* rowptr;
     const int32_t* colidx;
     const int32_t* rowidx;
@@ -362,7 +364,6 @@ struct Launch {
     int threads;
     bool chunks;       // balanced schedule
     bool ring;         // stage gathered rows in a shared-memory ring where the path has one
-    bool lean;         // the ring's lean form (tiles unrolled; SpMM, one vector per lane)
     int stages;        // batch slots of the ring (2 or 4)
 };
 

@@ -178,6 +178,10 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
     const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (vbase + gl) * 16;   // lane's first vector
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DTB);
     const bool vec_vals = a.vals_staged != 0;            // vals alone, 16-byte aligned
+    // several heads (NV = 1): the lane's columns belong to head (vector / vectors per head),
+    // whose value array starts hstride elements after the previous head's
+    const float* __restrict__ hvals = a.vals;
+    if (a.heads > 1 && a.vals) hvals += (int64_t)min((vbase + gl) / (nvec / a.heads), a.heads - 1) * a.hstride;
 
     float acc[NV][VECN];
 #pragma unroll
@@ -195,7 +199,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
     };
     auto value = [&](int e) {
         const int vi = a.vperm ? __ldg(a.vperm + e) : e;
-        float sv = a.vals ? __ldg(a.vals + vi) : 1.f;
+        float sv = hvals ? __ldg(hvals + vi) : 1.f;
         if (a.vals2) sv *= __ldg(a.vals2 + vi);
         return sv;
     };
@@ -226,7 +230,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             if (vec_vals) {
 #pragma unroll
                 for (int u = 0; u < U; u += 4) {
-                    const float4 v4 = __ldg(reinterpret_cast<const float4*>(a.vals + eb + u));
+                    const float4 v4 = __ldg(reinterpret_cast<const float4*>(hvals + eb + u));
                     s[u] = v4.x; s[u + 1] = v4.y; s[u + 2] = v4.z; s[u + 3] = v4.w;
                 }
             } else {

@@ -607,164 +607,4 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
     for (int rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
-// ----------------------------------------------------------------------------
-// SpMM, lean form of the ring span for one lane vector per row slice (NV = 1)
-// covering all of K: the same data flow and arithmetic as spmm_ring_span,
-// with the batches of each index tile unrolled so that ring slots, staged
-// offsets and shuffle source lanes are constants, shared-memory addresses
-// kept as 32-bit offsets, and the span checks confined to the first and last
-// tiles of the span (interior tiles hold only entries of the span).
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ void cpa_s(uint32_t saddr, const void* gmem, int bytes)
-{
-    if (bytes == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(gmem) : "memory");
-}
-
-template <int DT, int G, int U, int VB>
-__device__ __forceinline__ void spmm_lean_span(const SpmmArgs& a, const Group<G>& g, unsigned char* wsm, int kb, int nkb,
-                                               int r0, int e0, int r1, int e1, const int4 meta, int head_s0)
-{
-    using Vec = typename LaneVec<VB>::type;
-    constexpr int VECN = VB / dt_bytes(DT);
-    constexpr int NV = 1;
-    constexpr int TG = 4 * G;                       // entries per index tile (one int4 per lane)
-    constexpr int BPT = TG / U;                     // batches per tile
-    static_assert(U % 4 == 0 && BPT >= 2 && BPT % 2 == 0, "batches tile the index tile, slots alternate");
-    const int gl = g.gl;
-    const int lane = threadIdx.x & 31;
-    const int grp = lane / G;
-    const int nvec = a.K / VECN;
-    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(wsm) + (uint32_t)lane * VB;   // + (slot*U + u) * 32 * VB
-    const Vec* rv = reinterpret_cast<const Vec*>(wsm) + lane;
-    int* trow = reinterpret_cast<int*>(wsm + 2 * U * 32 * VB) + grp * TG;
-    float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wsm + 2 * U * 32 * VB) + 2 * 128) + grp * TG;
-    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (size_t)(kb * G + gl) * VB;
-    const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DT);
-    const float* __restrict__ vals = a.vals;
-
-    float acc[NV][VECN];
-#pragma unroll
-    for (int q = 0; q < VECN; ++q) acc[0][q] = 0.f;
-    int cur = r0;
-    auto flush = [&](int row) {
-        if (row == r0 && meta.x >= 0)
-            finish_piece<VECN, G, NV>(a, g, kb, nkb, nvec, meta.x, head_s0, row, acc);
-        else if (row == r1 && meta.y >= 0)
-            finish_piece<VECN, G, NV>(a, g, kb, nkb, nvec, meta.y, meta.y, row, acc);
-        else
-            write_row<VECN, G, NV>(a, g, kb, nvec, row, acc);
-    };
-    auto accumulate = [&](float sv, const Vec bvec) {
-        float bf[VECN];
-        unpack_vec<DT, VECN>(bvec, bf);
-        axpy_pairs<VECN>(acc[0], sv, bf);
-    };
-    // one entry of the slow path: close the current row on a row change
-    auto entry = [&](int r, float sv, const Vec bvec) {
-        if (r != cur) {
-            flush(cur);
-            for (int rr = cur + 1; rr < r; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
-            cur = r;
-#pragma unroll
-            for (int q = 0; q < VECN; ++q) acc[0][q] = 0.f;
-        }
-        accumulate(sv, bvec);
-    };
-
-    if (e0 < e1) {
-        const int tb0 = e0 & ~3;
-        const int ntile = (e1 - tb0 + TG - 1) / TG;
-        auto cols = [&](int t) -> int4 {
-            const int e = tb0 + t * TG + 4 * gl;
-            if (e + 4 <= e1) return ld4(a.colidx + e);
-            int4 c = make_int4(0, 0, 0, 0);
-            if (e < e1) c.x = __ldg(a.colidx + e);
-            if (e + 1 < e1) c.y = __ldg(a.colidx + e + 1);
-            if (e + 2 < e1) c.z = __ldg(a.colidx + e + 2);
-            return c;
-        };
-        auto stage = [&](int t) {                   // rows and values of tile t into buffer t & 1
-            const int e = tb0 + t * TG + 4 * gl;
-            const int n = e1 - e;
-            if (n <= 0) return;
-            const int bytes = n >= 4 ? 16 : 4 * n;
-            const int o = (t & 1) * 128 + 4 * gl;
-            cp_async16(trow + o, a.rowidx + e, bytes);
-            if (vals) cp_async16(tval + o, vals + e, bytes);
-        };
-        // gathers of batch bi (entries bi*U ..) of the tile whose columns are tc, into slot `slot`;
-        // entries at or past e1 are skipped
-        auto gather = [&](const int4 tc, const int bi, const int slot, const int ebase) {
-#pragma unroll
-            for (int c = 0; c < U / 4; ++c) {
-                const int src = bi * (U / 4) + c;
-                const int j0 = __shfl_sync(g.mask, tc.x, src, G);
-                const int j1 = __shfl_sync(g.mask, tc.y, src, G);
-                const int j2 = __shfl_sync(g.mask, tc.z, src, G);
-                const int j3 = __shfl_sync(g.mask, tc.w, src, G);
-                const int eq = ebase + bi * U + 4 * c;
-                const uint32_t d = ring + (uint32_t)((slot * U + 4 * c) * 32 * VB);
-                if (eq < e1) cpa_s(d, Bb + (size_t)(unsigned)j0 * ldb_bytes, VB);
-                if (eq + 1 < e1) cpa_s(d + 32 * VB, Bb + (size_t)(unsigned)j1 * ldb_bytes, VB);
-                if (eq + 2 < e1) cpa_s(d + 64 * VB, Bb + (size_t)(unsigned)j2 * ldb_bytes, VB);
-                if (eq + 3 < e1) cpa_s(d + 96 * VB, Bb + (size_t)(unsigned)j3 * ldb_bytes, VB);
-            }
-        };
-        int4 tc = cols(0), nc = cols(1);
-        stage(0);
-        gather(tc, 0, 0, tb0);
-        cp_async_commit();
-        for (int t = 0; t < ntile; ++t) {
-            const int et = tb0 + t * TG;            // first entry of tile t
-            const bool inner = (et >= e0) && (et + TG <= e1);
-            const int o = (t & 1) * 128;
-#pragma unroll
-            for (int bi = 0; bi < BPT; ++bi) {
-                __syncwarp(g.mask);
-                if (bi + 1 < BPT) {
-                    gather(tc, bi + 1, (bi + 1) & 1, et);
-                } else if (t + 1 < ntile) {
-                    tc = nc;
-                    nc = cols(t + 2);
-                    stage(t + 1);
-                    gather(tc, 0, 0, et + TG);
-                }
-                cp_async_commit();
-                cp_async_wait<1>();
-                __syncwarp(g.mask);
-                const int eb = et + bi * U;
-                const Vec* sl = rv + (bi & 1) * U * 32;
-                const int* rb = trow + o + bi * U;
-                const float* vb = tval + o + bi * U;
-                if (inner && rb[U - 1] == cur) {
-                    // the whole batch adds to the current row
-#pragma unroll
-                    for (int c = 0; c < U / 4; ++c) {
-                        float4 v4 = make_float4(1.f, 1.f, 1.f, 1.f);
-                        if (vals) v4 = *reinterpret_cast<const float4*>(vb + 4 * c);
-                        accumulate(v4.x, sl[(4 * c + 0) * 32]);
-                        accumulate(v4.y, sl[(4 * c + 1) * 32]);
-                        accumulate(v4.z, sl[(4 * c + 2) * 32]);
-                        accumulate(v4.w, sl[(4 * c + 3) * 32]);
-                    }
-                } else if (inner) {
-#pragma unroll 1
-                    for (int u = 0; u < U; ++u) entry(rb[u], vals ? vb[u] : 1.f, sl[u * 32]);
-                } else {
-                    const int u0 = max(e0 - eb, 0), u1 = min(e1 - eb, U);
-#pragma unroll 1
-                    for (int u = u0; u < u1; ++u) entry(rb[u], vals ? vb[u] : 1.f, sl[u * 32]);
-                }
-            }
-        }
-        cp_async_wait<0>();
-        __syncwarp(g.mask);
-    }
-    flush(cur);
-    for (int rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
-}
-
 }  // namespace spk

@@ -305,36 +305,6 @@ __global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(NV
     }
 }
 
-// Lean ring path (variant 4): one lane vector per row slice, all of K covered.
-template <int DT, int G, int U, int VB>
-__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(1, U, VB))) k_spmm_lean(const SpmmArgs a)
-{
-    extern __shared__ __align__(16) unsigned char ring_smem[];
-    const Group<G> g;
-    unsigned char* wsm = ring_smem + (threadIdx.x >> 5) * spmm_ring_bytes(1, U, VB);
-    const int kb = blockIdx.y, nkb = gridDim.y;
-    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    for (int64_t c = gid; c < a.nchunks; c += ngroups) {
-        const int2 b0 = a.bnd[c], b1 = a.bnd[c + 1];
-        const int4 m = a.meta[c];
-        if (b1.y == b0.y && m.z < b0.x) continue;          // nothing in this chunk
-        const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-        spmm_lean_span<DT, G, U, VB>(a, g, wsm, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
-    }
-}
-
-template <int DT, int VB>
-inline const void* spmm_lean_kernel_for(int shape)
-{
-    switch (shape) {
-#define X(i, G_, NV_, U_) case i: return NV_ == 1 ? (const void*)&k_spmm_lean<DT, G_, U_, VB> : nullptr;
-        SPK_SHAPES(X)
-#undef X
-    }
-    return nullptr;
-}
-
 template <int DT, int VB>
 inline const void* spmm_ring_kernel_for(int shape)
 {
@@ -380,13 +350,7 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
                                   : spmm_ring_kernel_for<DTB, 16>(L.shape);
             if (!rf) return cudaErrorInvalidValue;
             const int nkb2 = half ? (a.K / 4 + sh.G * sh.NV - 1) / (sh.G * sh.NV) : nkb;
-            // lean form: one vector per lane and every K block full
-            const int vecs = half ? a.K / 4 : nvec;
-            if (L.lean && sh.NV == 1 && vecs % sh.G == 0) {
-                const void* lf = half ? spmm_lean_kernel_for<DTB, (can_half ? 8 : 16)>(L.shape)
-                                      : spmm_lean_kernel_for<DTB, 16>(L.shape);
-                if (lf) rf = lf;
-            }
+
             const int64_t groups_per_cta = RING_THREADS / sh.G;
             int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
             if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;

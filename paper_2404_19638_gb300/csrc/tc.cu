@@ -150,8 +150,9 @@ __device__ __forceinline__ void load_rows_kmajor(unsigned char* dst, const __nv_
 }  // namespace
 
 // ----------------------------------------------------------------------------
-// SDDMM on dense tiles: one CTA per tile.  out[e] = s_e * (A_panel B_tile^T)[i, j]
-// for every entry e = (i, j) the plan lists for the tile.
+// SDDMM on dense tiles: one CTA per tile (several resident per SM, so one
+// tile's loads overlap another's product and sampling).
+//   out[e] = s_e * (A_panel B_tile^T)[i, j] for every entry e = (i, j) of the tile.
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS) k_tc_sddmm(const TcArgs a)
 {
@@ -183,9 +184,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_sddmm(const TcArgs a)
     if (threadIdx.x == 0) {
         const uint32_t idesc = idesc_bf16(TC_M, TC_N);
         const uint32_t kbytes = (uint32_t)K * 2;
-        for (int k = 0; k < K / 16; ++k)
+        for (int k = 0; k < K / 16; ++k)                      // K step 16 = two core columns of 128 bytes
             mma_bf16(tmem, kmajor_desc(smem_u32(sA) + 256 * k, kbytes), kmajor_desc(smem_u32(sB) + 256 * k, kbytes),
-                     idesc, k > 0);                            // K step 16 = two core columns of 128 bytes
+                     idesc, k > 0);
         mma_commit(bar);
     }
     const bool done = mbar_wait(bar, 0);
@@ -208,12 +209,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_sddmm(const TcArgs a)
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, TC_N);
     if (!done) return;
-    for (int q = threadIdx.x; q < tile.w; q += blockDim.x) {
-        const int64_t ent = (int64_t)tile.z + q;
-        const int32_t e = a.ent_slot[ent];
-        const int32_t ij = a.ent_ij[ent];
-        float s = a.vals ? a.vals[e] : 1.f;
-        a.out[e] = s * sD[(ij >> 16) * 65 + (ij & 0xffff)];
+    // sample the block: eight entries per thread at a time, every load of a
+    // round issued before its results are used
+    constexpr int R = 8;
+    for (int q0 = 0; q0 < tile.w; q0 += R * TC_THREADS) {
+        int32_t e[R], ij[R];
+        float sv[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int q = q0 + k * TC_THREADS + threadIdx.x;
+            const bool in = q < tile.w;
+            e[k] = in ? __ldg(a.ent_slot + tile.z + q) : -1;
+            ij[k] = in ? __ldg(a.ent_ij + tile.z + q) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) sv[k] = (a.vals && e[k] >= 0) ? __ldg(a.vals + e[k]) : 1.f;
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (e[k] >= 0) __stcs(a.out + e[k], sv[k] * sD[(ij[k] >> 16) * 65 + (ij[k] & 0xffff)]);
     }
 }
 

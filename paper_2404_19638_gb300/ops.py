@@ -128,6 +128,62 @@ def spmm_t(S: CSR, Y: torch.Tensor, vals=None, vals2=None, *, y_scale=None, out:
     return out
 
 
+def _head_vals(vals: torch.Tensor, S: CSR, heads: int) -> torch.Tensor:
+    if vals.dtype != torch.float32 or vals.device != S.device or vals.dim() != 2 or vals.shape != (heads, S.nnz) \
+            or vals.stride(1) != 1:
+        raise ValueError("vals must be float32, heads x nnz, rows contiguous, on the pattern's device")
+    return vals
+
+
+def spmm_mh(S: CSR, B: torch.Tensor, vals: torch.Tensor, heads: int, *, out: torch.Tensor | None = None,
+            accumulate: bool = False) -> torch.Tensor:
+    """C[:, head h] = S_h B[:, head h] with the values of head h in vals[h]
+    (heads x nnz): one pass over the pattern for all heads.  FP32 output."""
+    dtb, ldb = _dense(B, "B", S.device)
+    if B.size(0) != S.N:
+        raise ValueError(f"B has {B.size(0)} rows, S has {S.N} columns")
+    K = B.size(1)
+    vals = _head_vals(vals, S, heads)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs an output tensor")
+        out = torch.empty((S.M, K), dtype=torch.float32, device=S.device)
+    _, ldc = _dense(out, "out", S.device)
+    if out.dtype != torch.float32 or out.shape != (S.M, K):
+        raise ValueError("out must be M x K float32")
+    ws = S.workspace(K) if S.has_schedule else None
+    check(lib().spk_spmm_mh(S.handle, vals.data_ptr(), vals.stride(0), int(heads), dtb, B.data_ptr(), ldb, K,
+                            out.data_ptr(), ldc, int(accumulate), _ptr(ws), 0 if ws is None else ws.numel(),
+                            _stream(S.device)), "spk_spmm_mh")
+    return out
+
+
+def spmm_t_mh(S: CSR, Y: torch.Tensor, vals: torch.Tensor, heads: int, *, out: torch.Tensor | None = None,
+              accumulate: bool = False, plan: TransposePlan | None = None) -> torch.Tensor:
+    """X[:, head h] = S_h^T Y[:, head h] with the values of head h in vals[h]
+    (heads x nnz), through the transpose plan.  FP32 output."""
+    P = plan or S.transpose_plan()
+    dty, ldy = _dense(Y, "Y", S.device)
+    if Y.size(0) != S.M:
+        raise ValueError(f"Y has {Y.size(0)} rows, S has {S.M} rows")
+    K = Y.size(1)
+    vals = _head_vals(vals, S, heads)
+    if out is None:
+        if accumulate:
+            raise ValueError("accumulate needs an output tensor")
+        out = torch.empty((S.N, K), dtype=torch.float32, device=S.device)
+    _, ldx = _dense(out, "out", S.device)
+    if out.dtype != torch.float32 or out.shape != (S.N, K):
+        raise ValueError("out must be N x K float32")
+    n = ctypes.c_size_t()
+    check(lib().spk_spmm_t_mh_workspace_size(P.handle, K, int(heads), ctypes.byref(n)), "spk_spmm_t_mh_workspace_size")
+    ws = P.mh_workspace(n.value)
+    check(lib().spk_spmm_t_mh(P.handle, vals.data_ptr(), vals.stride(0), int(heads), dty, Y.data_ptr(), ldy, K,
+                              out.data_ptr(), ldx, int(accumulate), ws.data_ptr(), ws.numel(), _stream(S.device)),
+          "spk_spmm_t_mh")
+    return out
+
+
 def fusedmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, *, heads: int = 1, scale: float = 1.0,
             softmax: bool = False, want_scores: bool = False, want_lse: bool = False,
             out: torch.Tensor | None = None, tune=None, use_default_vals: bool = True):

@@ -237,6 +237,14 @@ class TransposePlan:
 
         return view(cp, self.N + 1), view(ri, self.nnz), view(pm, self.nnz)
 
+    def mh_workspace(self, nbytes: int) -> torch.Tensor:
+        """Workspace of a multi-head S^T Y (cached, grown on demand)."""
+        ws = self._ws.get("mh")
+        if ws is None or ws.numel() < nbytes:
+            ws = _buffer(nbytes, self.S.device)
+            self._ws["mh"] = ws
+        return ws
+
     def workspace(self, K: int) -> torch.Tensor | None:
         nbytes = ctypes.c_size_t()
         check(lib().spk_spmm_t_workspace_size(self._h, int(K), ctypes.byref(nbytes)), "spk_spmm_t_workspace_size")

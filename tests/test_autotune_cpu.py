@@ -6,16 +6,18 @@ import numpy as np
 import torch
 
 import synth
-from paper_2404_19638_gb300.autotune import _COMPILED, candidate_shapes, pattern_signature
+from paper_2404_19638_gb300.autotune import candidate_shapes, pattern_signature
+from paper_2404_19638_gb300.binding import compiled_shapes
 
 ROOT = Path(__file__).resolve().parents[1]
 
 
 def test_candidates_are_compiled_shapes():
+    """The library reports the shape table its kernels were compiled from."""
     src = (ROOT / "paper_2404_19638_gb300" / "csrc" / "common.cuh").read_text()
     block = src[src.index("#define SPK_SHAPES"):src.index("constexpr int kNumShapes")]
-    compiled = {tuple(int(v) for v in m) for m in re.findall(r"X\(\d+,\s*(\d+),\s*(\d+),\s*(\d+)\)", block)}
-    assert compiled == _COMPILED
+    compiled = [tuple(int(v) for v in m) for m in re.findall(r"X\(\d+,\s*(\d+),\s*(\d+),\s*(\d+)\)", block)]
+    assert compiled_shapes() == compiled
 
 
 def test_candidates_cover_the_row():
@@ -25,7 +27,7 @@ def test_candidates_cover_the_row():
             cands = candidate_shapes(K, dt)
             assert cands
             for G, NV, U in cands:
-                assert (G, NV, U) in _COMPILED
+                assert (G, NV, U) in compiled_shapes()
                 assert G * NV >= min(nvec, 128) or (G, NV, U) == (32, 4, 4)
 
 

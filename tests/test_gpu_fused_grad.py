@@ -181,3 +181,41 @@ def test_fusedmm_grad_matches_unfused_composition(spk):
         assert comp_err(y.cpu().numpy(), ref, den) <= GRAD_TOL
         assert comp_err(x.cpu().numpy(), y.double().cpu().numpy(), den) <= 2 * GRAD_TOL
         assert _normwise(x.cpu().numpy(), y.double().cpu().numpy()) <= NORM_TOL
+
+
+@pytest.mark.parametrize("heads,K,dt", [(4, 64, torch.float32), (2, 32, torch.float32), (3, 24, torch.float32),
+                                        (4, 128, torch.float32), (4, 64, torch.bfloat16), (8, 256, torch.float32)])
+def test_multi_head_spmm_and_spmm_t(spk, heads, K, dt):
+    """One pass for all heads: C[:, head h] = S_h B[:, head h] and
+    X[:, head h] = S_h^T Y[:, head h], each head with its own values, against
+    the oracle head by head (componentwise, FP32 accumulation)."""
+    M, N = 700, 520
+    rp, ci = edge_pattern(M, N, seed=61 + heads + K, long_row=2200)
+    g = np.random.default_rng(K + heads)
+    S = spk.CSR(rp, ci, (M, N), device=DEV, chunk_work=128)
+    V = g.uniform(-1, 1, (heads, ci.size)).astype(np.float32)
+    B = g.standard_normal((N, K)).astype(np.float32)
+    Y = g.standard_normal((M, K)).astype(np.float32)
+    tB = torch.from_numpy(B).to(DEV).to(dt)
+    tY = torch.from_numpy(Y).to(DEV).to(dt)
+    tV = torch.from_numpy(V).to(DEV)
+    C = spk.ops.spmm_mh(S, tB, tV, heads).cpu().numpy()
+    X = spk.ops.spmm_t_mh(S, tY, tV, heads).cpu().numpy()
+    if dt == torch.bfloat16:
+        Bo, Yo, kb, ky = (tB.view(torch.int16).cpu().numpy().view(np.uint16),
+                          tY.view(torch.int16).cpu().numpy().view(np.uint16), {"fmt_b": "bf16"}, {"fmt_y": "bf16"})
+    else:
+        Bo, Yo, kb, ky = B, Y, {}, {}
+    Kh = K // heads
+    for h in range(heads):
+        sl = slice(h * Kh, (h + 1) * Kh)
+        Bh, Yh = np.ascontiguousarray(Bo[:, sl]), np.ascontiguousarray(Yo[:, sl])
+        assert comp_err(C[:, sl], oracle.spmm(rp, ci, Bh, V[h], **kb),
+                        oracle.spmm(rp, ci, Bh, V[h], absmode=True, **kb)) <= TOL
+        assert comp_err(X[:, sl], oracle.spmm_t(rp, ci, N, Yh, V[h], **ky),
+                        oracle.spmm_t(rp, ci, N, Yh, V[h], absmode=True, **ky)) <= TOL
+    # accumulate mode adds onto the output
+    base = torch.from_numpy(g.standard_normal((M, K)).astype(np.float32)).to(DEV)
+    acc = base.clone()
+    spk.ops.spmm_mh(S, tB, tV, heads, out=acc, accumulate=True)
+    np.testing.assert_allclose(acc.cpu().numpy(), base.cpu().numpy() + C, rtol=1e-6, atol=1e-5)

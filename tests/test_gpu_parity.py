@@ -36,13 +36,13 @@ SHAPES = [(4, 1, 4), (8, 1, 8), (16, 1, 8), (32, 1, 8), (8, 2, 8), (16, 2, 8), (
 
 
 @pytest.mark.parametrize("K", [1, 3, 8, 24, 32, 40, 64, 128, 136])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, "stages4"])
 def test_sddmm_spmm_f32_k_sweep(spk, K, variant):
     M, N = 700, 500
     rp, ci, vals, A, B = _case(M, N, K, seed=K, long_row=3000)
     S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV, chunk_work=128)
     tA, tB = torch.from_numpy(A).to(DEV), torch.from_numpy(B).to(DEV)
-    tune = {"variant": variant} if variant < 4 else {"variant": 2, "stages": 4}
+    tune = {"variant": 2, "stages": 4} if variant == "stages4" else {"variant": variant}
     out = spk.sddmm(S, tA, tB, tune=tune).cpu().numpy()
     C = spk.spmm(S, tB, tune=tune).cpu().numpy()
     X = spk.spmm_t(S, tA, tune=tune).cpu().numpy()
