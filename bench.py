@@ -327,7 +327,9 @@ def reference_arm(args):
         return 0
     if args.workload == "batch":
         return reference_arm_batch(args)
-    P, desc = load_workload(args.workload)
+    # the relabelling and dense-tile workloads compute the rmat20 step and a
+    # plain SDDMM: the oracle's reference for them is that of rmat20
+    P, desc = load_workload("rmat20" if args.workload in ("reorder", "blocks") else args.workload)
     import oracle
     oracle.build()
     if P.vals is not None:          # the oracle takes values in FP64 (exact from FP32): convert once, untimed
@@ -524,6 +526,10 @@ def main(args):
         return reference_arm(args)
     if args.workload == "batch":
         return main_batch(args)
+    if args.workload == "reorder":
+        return main_reorder(args)
+    if args.workload == "blocks":
+        return main_blocks(args)
 
     import torch
     import torch.distributed as dist
@@ -956,13 +962,94 @@ def main_batch(args):
     return 0
 
 
+REORDER_DESC = ("reorder: rmat20 (R-MAT scale 20, edge factor 16, values U[-1,1], A, B 2^20 x 64 N(0,1) FP32) "
+                "with its rows relabelled (degree, leading column, reverse Cuthill-McKee) vs the original order")
+BLOCKS_DESC = ("blocks: 131,072 x 131,072, 1500 fully dense 128 x 64 blocks at aligned positions over 2 uniform "
+               "columns per row, values U[-1,1]; A, B N(0,1) in BF16")
+
+
+def _single_gpu_line(args, metric_value, ms, desc, extra, dtype):
+    import torch
+    return {"metric": METRIC, "value": metric_value, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": desc, "l2": "flushed before every timed launch (256 MB write)",
+                       "parallelism": "single GPU"}, **extra}
+
+
+def main_reorder(args):
+    """Step time of rmat20 in each row order (the relabelled pattern keeps the
+    original column ids; A is gathered into the new row order once)."""
+    import torch
+    import paper_2404_19638_gb300 as spk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P, _ = load_workload("rmat20")
+    vals = torch.from_numpy(P.vals).to(dev)
+    S = spk.CSR(P.rowptr, P.colidx, (P.M, P.N), vals, device=dev)
+    A = torch.from_numpy(P.A).to(dev)
+    B = torch.from_numpy(P.B).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    reps = max(args.steps, 5)
+    res = {"original": {"sddmm_ms": event_ms(lambda: spk.sddmm(S, A, B), stream, flush, reps),
+                        "spmm_ms": event_ms(lambda: spk.spmm(S, B), stream, flush, reps)}}
+    for order in ("degree", "leading", "rcm"):
+        t0 = time.perf_counter()
+        R = spk.Reordering(S, order)
+        torch.cuda.synchronize(dev)
+        build = time.perf_counter() - t0
+        Ar = R.gather_rows(A)
+        res[order] = {"plan_build_s": build, "sddmm_ms": event_ms(lambda: spk.sddmm(R.S, Ar, B), stream, flush, reps),
+                      "spmm_ms": event_ms(lambda: spk.spmm(R.S, B), stream, flush, reps),
+                      "gather_rows_ms": event_ms(lambda: R.gather_rows(A), stream, flush, reps),
+                      "scatter_values_ms": event_ms(lambda: R.scatter_values(vals), stream, flush, reps)}
+    best = min(("degree", "leading", "rcm"), key=lambda o: res[o]["sddmm_ms"] + res[o]["spmm_ms"])
+    ms = res[best]["sddmm_ms"] + res[best]["spmm_ms"]
+    line = _single_gpu_line(args, 2.0 * 2.0 * P.nnz * P.K / (ms / 1e3) / 1e9, ms, REORDER_DESC,
+                            {"reorder": res, "best_order": best, "gpu_launches": 2 * reps}, "f32")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main_blocks(args):
+    """SDDMM of a pattern with dense blocks: the tensor-core tiles plus the
+    gather kernels on the rest, against the gather kernels on everything."""
+    import torch
+    import paper_2404_19638_gb300 as spk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1 << 17
+    rp, ci = synth.dense_blocks(n, n, 1500, 1.0, 2, seed=3)
+    vals = torch.from_numpy(synth.uniform(ci.size, -1.0, 1.0, 3, 9)).to(dev)
+    S = spk.CSR(rp, ci, (n, n), vals, device=dev)
+    t0 = time.perf_counter()
+    plan = spk.TensorCorePlan(S, 1024)
+    torch.cuda.synchronize(dev)
+    build = time.perf_counter() - t0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    reps = max(args.steps, 5)
+    res = {"plan": plan.info(), "plan_build_s": build}
+    for K in (64, 128, 256):
+        A = torch.from_numpy(synth.normal((n, K), 1.0, 3, 2)).to(dev).to(torch.bfloat16)
+        B = torch.from_numpy(synth.normal((n, K), 1.0, 3, 3)).to(dev).to(torch.bfloat16)
+        g = event_ms(lambda: spk.sddmm(S, A, B), stream, flush, reps)
+        t = event_ms(lambda: spk.tc_sddmm(plan, A, B), stream, flush, reps)
+        res[f"K{K}"] = {"gather_sddmm_ms": g, "tc_sddmm_ms": t, "speedup": g / t,
+                        "tc_gflops": 2.0 * ci.size * K / (t / 1e3) / 1e9}
+    ms = res["K128"]["tc_sddmm_ms"]
+    line = _single_gpu_line(args, res["K128"]["tc_gflops"], ms, BLOCKS_DESC,
+                            {"tc": res, "op": "SDDMM (K = 128 for the value)", "gpu_launches": 3 * reps}, "bf16")
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn", "batch"])
+    ap.add_argument("--workload", default="rmat20", choices=["rmat20", "tiny", "rec", "gnn", "batch", "reorder", "blocks"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--chunk-work", type=int, default=None,
                     help="balanced-schedule chunk size (default 512; 128 for the batched workload)")

@@ -510,7 +510,7 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
                 heads);
         const int G = nv <= 4 ? 4 : (nv <= 8 ? 8 : (nv <= 16 ? 16 : 32));
         spk_tune t{};
-        t.variant = S->has_sched ? 3 : 1;
+        t.variant = S->has_sched ? 2 : 1;
         t.group_lanes = G;
         t.vecs_per_lane = 1;
         t.unroll = G == 4 ? 4 : 8;
@@ -531,7 +531,9 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
     a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
     a.vperm = vals_in_slot_order ? nullptr : S->vperm;
     a.vals = vals; a.vals2 = vals2;
-    a.vals_staged = (vals && !vals2 && !a.vperm && aligned16(vals) && (heads == 1 || hstride % 4 == 0)) ? 1 : 0;
+    // staged values: through the index tiles (several heads: one pair of
+    // tiles each; a head array off 16-byte alignment is staged 4 bytes at a time)
+    a.vals_staged = (vals && !vals2 && !a.vperm && aligned16(vals)) ? 1 : 0;
     a.heads = heads;
     a.hstride = hstride;
     a.B = B; a.ldb = ldb; a.b_scale = b_scale;

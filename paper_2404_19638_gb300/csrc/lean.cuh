@@ -177,7 +177,8 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
     const bool all_vin = (nvec >= vbase + G * NV);
     const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + (vbase + gl) * 16;   // lane's first vector
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DTB);
-    const bool vec_vals = a.vals_staged != 0;            // vals alone, 16-byte aligned
+    // vals alone and 16-byte aligned (every head's array too)
+    const bool vec_vals = a.vals_staged != 0 && (a.heads == 1 || (a.hstride & 3) == 0);
     // several heads (NV = 1): the lane's columns belong to head (vector / vectors per head),
     // whose value array starts hstride elements after the previous head's
     const float* __restrict__ hvals = a.vals;

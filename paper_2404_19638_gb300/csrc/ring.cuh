@@ -369,9 +369,11 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
 // ----------------------------------------------------------------------------
 // VB: bytes of one lane vector, 16, or 8 for 16-bit operands spread over
 // twice the lanes (a group of G lanes then covers G * NV * VB bytes of a row).
-__host__ __device__ constexpr int spmm_ring_bytes(int NV, int U, int VB = 16)
+// Per warp: two batch slots of gathered rows, the staged COO rows (two tiles
+// of 128 entries) and the staged values (two tiles per head).
+__host__ __device__ constexpr int spmm_ring_bytes(int NV, int U, int VB = 16, int heads = 1)
 {
-    return 2 * U * NV * 32 * VB + 2 * 2 * 128 * 4;
+    return 2 * U * NV * 32 * VB + 2 * 128 * 4 + heads * 2 * 128 * 4;
 }
 
 __device__ __forceinline__ void cpa8(void* smem, const void* gmem)
@@ -426,6 +428,10 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
     // group grp owns entries [grp * 4G, (grp + 1) * 4G) of each 128-entry buffer
     int* trow = reinterpret_cast<int*>(wring + 2 * U * NV * 32) + grp * TG;
     float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wring + 2 * U * NV * 32) + 2 * 128) + grp * TG;
+    // several heads (NV = 1): head h's values in the h-th pair of value tiles;
+    // this lane reads the tiles of the head its columns belong to
+    float* tval_l = tval;
+    if (a.heads > 1) tval_l += min((vbase + gl) / (nvec / a.heads), a.heads - 1) * 256;
 
     float acc[NV][VECN];
 #pragma unroll
@@ -461,7 +467,21 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
             const int bytes = n >= 4 ? 16 : 4 * n;
             const int o = (t & 1) * 128 + 4 * gl;
             cp_async16(trow + o, a.rowidx + e, bytes);
-            if (vals) cp_async16(tval + o, vals + e, bytes);
+            if (vals) {
+                if (a.heads == 1) {
+                    cp_async16(tval + o, vals + e, bytes);
+                } else {
+                    for (int h = 0; h < a.heads; ++h) {
+                        const float* hv = vals + (int64_t)h * a.hstride + e;
+                        if ((a.hstride & 3) == 0) {
+                            cp_async16(tval + h * 256 + o, hv, bytes);
+                        } else {                    // a head array off 16-byte alignment: four 4-byte copies
+                            const int n4 = n >= 4 ? 4 : n;
+                            for (int q = 0; q < n4; ++q) cpa4(tval + h * 256 + o + q, hv + q);
+                        }
+                    }
+                }
+            }
         };
         int4 tc = cols(0), nc = cols(1);
         int itile = 0;
@@ -532,7 +552,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                 const int4 r4 = *reinterpret_cast<const int4*>(trow + o + 4 * c);
                 rc[4 * c + 0] = r4.x; rc[4 * c + 1] = r4.y; rc[4 * c + 2] = r4.z; rc[4 * c + 3] = r4.w;
                 if (vals) {
-                    const float4 v4 = *reinterpret_cast<const float4*>(tval + o + 4 * c);
+                    const float4 v4 = *reinterpret_cast<const float4*>(tval_l + o + 4 * c);
                     sc[4 * c + 0] = v4.x; sc[4 * c + 1] = v4.y; sc[4 * c + 2] = v4.z; sc[4 * c + 3] = v4.w;
                 } else {
                     sc[4 * c + 0] = sc[4 * c + 1] = sc[4 * c + 2] = sc[4 * c + 3] = 1.f;
@@ -567,7 +587,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
 #pragma unroll
                             for (int q = 0; q < VECN; ++q) acc[t][q] = 0.f;
                     }
-                    const float sv = vals ? tval[o + u] : 1.f;
+                    const float sv = vals ? tval_l[o + u] : 1.f;
 #pragma unroll
                     for (int t = 0; t < NV; ++t) {
                         if (!vin[t]) continue;

@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(spmm_ring_bytes(NV
 {
     extern __shared__ __align__(16) unsigned char ring_smem[];
     const Group<G> g;
-    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (spmm_ring_bytes(NV, U, VB) / 16);
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (spmm_ring_bytes(NV, U, VB, a.heads) / 16);
     const int kb = blockIdx.y, nkb = gridDim.y;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -339,7 +339,8 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
     const int64_t items = a.bnd ? a.nchunks : a.M;
     if (items <= 0) return cudaSuccess;
     if constexpr (DTB != DT_E4M3) {
-        const bool ring_ok = L.vec && L.ring && a.bnd && !a.vperm && !a.vals2 && (!a.vals || a.vals_staged);
+        const bool ring_ok = L.vec && L.ring && a.bnd && !a.vperm && !a.vals2 && (!a.vals || a.vals_staged) &&
+                             (a.heads == 1 || shape_at(L.shape).NV == 1);
         if (ring_ok) {
             // 16-bit operands whose 16-byte vectors would leave half the group's
             // lanes idle are spread over all of them as 8-byte vectors
@@ -355,7 +356,7 @@ cudaError_t launch_spmm_t(const Launch& L, const SpmmArgs& a, cudaStream_t s)
             int64_t blocks = (items + groups_per_cta - 1) / groups_per_cta;
             if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
             if (nkb2 > 65535) return cudaErrorInvalidValue;
-            const size_t smem = (size_t)(RING_THREADS / 32) * spmm_ring_bytes(sh.NV, sh.U, vb);
+            const size_t smem = (size_t)(RING_THREADS / 32) * spmm_ring_bytes(sh.NV, sh.U, vb, a.heads);
             if (smem > 48 * 1024) {
                 cudaError_t e = cudaFuncSetAttribute(rf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
