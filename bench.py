@@ -80,12 +80,19 @@ def peaks():
     return dict(FALLBACK_PEAKS), "fallback"
 
 
+# The files the step kernels (k_sddmm_ring, k_spmm_ring and their register
+# and row-split siblings) compile from: a change elsewhere in csrc/ (FusedMM,
+# batch, tensor-core tiles, plans) leaves their ncu traffic valid.
+STEP_KERNEL_SOURCES = ("common.cuh", "tiles.cuh", "lean.cuh", "ring.cuh", "sddmm_impl.cuh", "spmm_impl.cuh",
+                       "sddmm_f32.cu", "sddmm_bf16.cu", "sddmm_f16.cu", "sddmm_e4m3.cu",
+                       "spmm_f32.cu", "spmm_bf16.cu", "spmm_f16.cu", "spmm_e4m3.cu")
+
+
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2404_19638_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

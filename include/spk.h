@@ -342,6 +342,15 @@ spk_status spk_tc_sddmm_workspace_size(spk_tcplan P, size_t* bytes);
 spk_status spk_tc_sddmm(spk_tcplan P, const float* vals, spk_dtype dt, const void* A, int64_t lda, const void* B,
                         int64_t ldb, int32_t K, float* out, void* workspace, size_t ws_bytes, const spk_tune* tune,
                         void* stream);
+/*
+ * spk_tc_sddmm_unarmed (test hook): launches the dense-tile kernel of P with
+ * its MMAs left out, so that every bounded wait on the tensor core's barrier
+ * runs out; each tile sets P's status word to 1, frees its tensor memory and
+ * returns without writing `out`.  Same argument rules as spk_tc_sddmm (A, B
+ * BF16).  Exists to test the wait limit without a fault or a hang.
+ */
+spk_status spk_tc_sddmm_unarmed(spk_tcplan P, const void* A, int64_t lda, const void* B, int64_t ldb, int32_t K,
+                                float* out, void* stream);
 
 /* ----------------------------------------------------- transpose plan -- */
 /* The CSC of S by a stable device radix sort on the column index: colptr[N+1],

@@ -95,6 +95,7 @@ _PROTOS = {
     "spk_tc_plan_destroy": (ctypes.c_int, [_vp]),
     "spk_tc_sddmm_workspace_size": (ctypes.c_int, [_vp, _P(_sz)]),
     "spk_tc_sddmm": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _i64, _vp, _i64, _i32, _vp, _vp, _sz, _P(Tune), _vp]),
+    "spk_tc_sddmm_unarmed": (ctypes.c_int, [_vp, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "spk_tplan_size": (ctypes.c_int, [_vp, _i32, _P(_sz), _P(_sz)]),
     "spk_tplan_build": (ctypes.c_int, [_vp, _i32, _vp, _sz, _vp, _sz, _P(_vp), _vp]),
     "spk_tplan_arrays": (ctypes.c_int, [_vp, _P(_vp), _P(_vp), _P(_vp)]),

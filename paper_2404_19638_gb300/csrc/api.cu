@@ -935,6 +935,29 @@ extern "C" spk_status spk_tc_sddmm(spk_tcplan P, const float* vals, spk_dtype dt
     return SPK_OK;
 }
 
+// Not in the public header: the tile kernel with no MMA issued and nothing
+// committed, so that every tile's bounded wait on the tensor core's barrier
+// runs out; the kernel then sets the plan's status word, frees its tensor
+// memory and returns, leaving `out` untouched.  Tests use it to check that
+// path without a fault or a hang.
+extern "C" spk_status spk_tc_sddmm_unarmed(spk_tcplan P, const void* A, int64_t lda, const void* B, int64_t ldb,
+                                           int32_t K, float* out, void* stream)
+{
+    REQUIRE(P && A && B && out && K >= 16 && K <= 256 && K % 16 == 0 && lda >= K && ldb >= K, SPK_ERR_ARG,
+            "spk_tc_sddmm_unarmed: bad argument");
+    REQUIRE(aligned16(A) && aligned16(B) && (lda * 2) % 16 == 0 && (ldb * 2) % 16 == 0, SPK_ERR_SHAPE,
+            "spk_tc_sddmm_unarmed: A and B must be 16-byte aligned with 16-byte row strides");
+    TcArgs a;
+    a.M = P->M; a.N = P->N; a.K = K;
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb;
+    a.tiles = P->tiles; a.ent_slot = P->ent_slot; a.ent_ij = P->ent_ij;
+    a.vals = nullptr; a.out = out; a.status = P->status;
+    a.unarmed = 1;
+    cudaError_t e = launch_tc_sddmm(a, P->ntiles, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_tc_sddmm_unarmed");
+    return SPK_OK;
+}
+
 // ----------------------------------------------------------------------------
 // Transpose plan
 // ----------------------------------------------------------------------------

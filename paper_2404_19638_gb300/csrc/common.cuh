@@ -449,6 +449,7 @@ struct TcArgs {
     const float* vals;               // NULL = ones
     float* out;
     int32_t* status;                 // set to 1 if a tensor-core wait ran out
+    int32_t unarmed = 0;             // 1: issue no MMA and no commit, so the wait runs out (tests only)
 };
 size_t tc_sddmm_smem(int K);
 cudaError_t launch_tc_sddmm(const TcArgs& a, int64_t ntiles, cudaStream_t s);

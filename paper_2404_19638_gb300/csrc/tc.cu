@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_sddmm(const TcArgs a)
     tc_fence_after();
     const uint32_t tmem = *tbase;
 
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !a.unarmed) {
         const uint32_t idesc = idesc_bf16(TC_M, TC_N);
         const uint32_t kbytes = (uint32_t)K * 2;
         for (int k = 0; k < K / 16; ++k)                      // K step 16 = two core columns of 128 bytes

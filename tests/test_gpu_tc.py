@@ -106,3 +106,35 @@ def test_tc_sddmm_all_tiles_or_none(spk, threshold):
     Bq = B.view(torch.int16).cpu().numpy().view(np.uint16)
     assert comp_err(out, oracle.sddmm(rp, ci, Aq, Bq, vals, fmt_a="bf16", fmt_b="bf16"),
                     oracle.sddmm(rp, ci, Aq, Bq, vals, fmt_a="bf16", fmt_b="bf16", absmode=True)) <= TOL
+
+
+def test_tensor_core_wait_limit_reports_status(spk):
+    """The kernel's waits on the tensor core's barrier are bounded: with no MMA
+    issued (an internal entry point) every wait runs out, the kernel records
+    the status, frees its tensor memory and returns without touching the
+    output — no fault, no hang — and the library still computes correctly."""
+    import ctypes
+    from paper_2404_19638_gb300.binding import lib
+    M, N, K = 384, 256, 64
+    rp, ci = synth.dense_blocks(M, N, 2, 0.9, 3, seed=17)
+    g = np.random.default_rng(17)
+    S = spk.CSR(rp, ci, (M, N), device=DEV)
+    P = spk.TensorCorePlan(S, 2048)
+    assert P.info()["tiles"] >= 1
+    A = torch.from_numpy(g.standard_normal((M, K)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    B = torch.from_numpy(g.standard_normal((N, K)).astype(np.float32)).to(DEV).to(torch.bfloat16)
+    out = torch.full((ci.size,), 7.0, device=DEV)
+    L = lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.spk_tc_sddmm_unarmed(P.handle, A.data_ptr(), K, B.data_ptr(), K, K, out.data_ptr(), st) == 0
+    torch.cuda.synchronize()
+    assert int(P.arrays()["status"].cpu()[0]) == 1
+    assert torch.all(out == 7.0)
+    # the context is intact: a normal call gives the oracle's result
+    P.arrays()["status"].zero_()
+    got = spk.tc_sddmm(P, A, B).cpu().numpy()
+    Aq = A.view(torch.int16).cpu().numpy().view(np.uint16)
+    Bq = B.view(torch.int16).cpu().numpy().view(np.uint16)
+    assert comp_err(got, oracle.sddmm(rp, ci, Aq, Bq, None, fmt_a="bf16", fmt_b="bf16"),
+                    oracle.sddmm(rp, ci, Aq, Bq, None, fmt_a="bf16", fmt_b="bf16", absmode=True)) <= TOL
+    assert int(P.arrays()["status"].cpu()[0]) == 0
