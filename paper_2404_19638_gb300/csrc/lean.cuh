@@ -162,9 +162,6 @@ __device__ __forceinline__ void write_row(const SpmmArgs& a, const Group<G>& g, 
 template <int VECN, int G, int NV>
 __device__ __forceinline__ void zero_row(const SpmmArgs& a, const Group<G>& g, int kb, int nvec, int64_t row);
 template <int VECN, int G, int NV>
-__device__ __forceinline__ void zero_rows(const SpmmArgs& a, const Group<G>& g, int kb, int nvec, int64_t r0,
-                                          int64_t r1);
-template <int VECN, int G, int NV>
 __device__ __forceinline__ void finish_piece(const SpmmArgs& a, const Group<G>& g, int kb, int nkb, int nvec,
                                              int slot, int s0, int64_t row, const float (&acc)[NV][VECN]);
 
@@ -269,7 +266,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
             if constexpr (!KNOWN_ROW) {
                 if (row[u] != cur) {
                     flush(cur);
-                    zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, row[u]);
+                    for (int rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
                     cur = row[u];
 #pragma unroll
                     for (int t = 0; t < NV; ++t)
@@ -291,7 +288,7 @@ __device__ __forceinline__ void spmm_group_span(const SpmmArgs& a, const Group<G
         }
     }
     flush(cur);
-    zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, (int64_t)meta.z + 1);
+    for (int rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
 }  // namespace spk

@@ -580,7 +580,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                     const int r = trow[o + u];
                     if (r != cur) {
                         flush(cur);
-                        zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, r);
+                        for (int rr = cur + 1; rr < r; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
                         cur = r;
 #pragma unroll
                         for (int t = 0; t < NV; ++t)
@@ -603,7 +603,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                     if (e < e0 || e >= e1) continue;
                     if (rc[u] != cur) {
                         flush(cur);
-                        zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, rc[u]);
+                        for (int rr = cur + 1; rr < rc[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
                         cur = rc[u];
 #pragma unroll
                         for (int t = 0; t < NV; ++t)
@@ -624,7 +624,7 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
         __syncwarp(g.mask);
     }
     flush(cur);
-    zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, (int64_t)meta.z + 1);
+    for (int rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
 }  // namespace spk

@@ -81,32 +81,6 @@ __device__ __forceinline__ void zero_row(const SpmmArgs& a, const Group<G>& g, i
     }
 }
 
-// Rows r0 .. r1-1 (rows without entries) written as zero: the output dtype
-// is decided once for the run of rows; a row is VECN * dt bytes per lane slot.
-template <int VECN, int G, int NV>
-__device__ __forceinline__ void zero_rows(const SpmmArgs& a, const Group<G>& g, int kb, int nvec, int64_t r0,
-                                          int64_t r1)
-{
-    if (a.accumulate || r0 >= r1) return;
-    float z[VECN];
-#pragma unroll
-    for (int q = 0; q < VECN; ++q) z[q] = 0.f;
-    const int ob = a.dtc == DT_F32 ? 4 : 2;
-    char* base = reinterpret_cast<char*>(a.C);
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-        const int v = kb * G * NV + t * G + g.gl;
-        if (v >= nvec) continue;
-        char* p = base + (r0 * a.ldc + (int64_t)v * VECN) * ob;
-        const int64_t step = a.ldc * ob;
-        if (ob == 4) {
-            for (int64_t r = r0; r < r1; ++r, p += step) store_elems<DT_F32, VECN>(p, 0, z);
-        } else {
-            for (int64_t r = r0; r < r1; ++r, p += step) store_elems<DT_BF16, VECN>(p, 0, z);   // zero bits in both 16-bit formats
-        }
-    }
-}
-
 // Deposit one piece of a split row and, if it is the last to arrive, finish the row.
 template <int VECN, int G, int NV>
 __device__ __forceinline__ void finish_piece(const SpmmArgs& a, const Group<G>& g, int kb, int nkb, int nvec,
@@ -250,7 +224,7 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
                 if constexpr (!KNOWN_ROW) {
                     if (row[u] != cur) {
                         flush(cur);
-                        zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, row[u]);
+                        for (int64_t rr = cur + 1; rr < row[u]; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
                         cur = row[u];
 #pragma unroll
                         for (int t2 = 0; t2 < NV; ++t2)
@@ -270,7 +244,7 @@ __device__ __forceinline__ void spmm_span(const SpmmArgs& a, const Group<G>& g, 
     }
     cp_async_wait<0>();
     flush(cur);
-    zero_rows<VECN, G, NV>(a, g, kb, nvec, cur + 1, (int64_t)meta.z + 1);
+    for (int64_t rr = cur + 1; rr <= meta.z; ++rr) zero_row<VECN, G, NV>(a, g, kb, nvec, rr);
 }
 
 // One group per span (a chunk of the balanced schedule, or a row).  The
