@@ -846,7 +846,9 @@ def main_batch(args):
         h2d += p.A.nbytes + p.B.nbytes + p.vals.nbytes
         d2h += out.numel() * 4 + C.numel() * 4
     batch = spk.Batch(items)
-    tuned = batch.autotune((64, 128, 256, 512))        # one chunk size for the batch, by timing
+    t0 = time.perf_counter()
+    tuned = batch.autotune((64, 128, 256, 512), per_item=True)     # schedules, shapes, registers, by timing
+    tune_s = time.perf_counter() - t0
     batch.capture()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -932,6 +934,11 @@ def main_batch(args):
                    "launch": "one persistent kernel per step, replayed from a CUDA graph",
                    "chunk_work": tuned["chunk_work"],
                    "autotune_ms": {str(k): round(v, 4) for k, v in tuned["ms"].items()},
+                   "autotune": {"chunk_work_by_nnz": tuned["chunk_work_by_nnz"],
+                                "shapes": {k: v for k, v in tuned["shapes"].items()},
+                                "registers": tuned["registers"], "ms_final": round(tuned["ms_final"], 4),
+                                "trials": tuned["trials"], "seconds": round(tune_s, 1),
+                                "note": "per-item choices by whole-launch timing; shape null = default by K"},
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "kernels": {"batch_ms": ms, "per_matrix_launches_ms": per_ms, "per_matrix_launches": 2 * len(keep),
                     "work_units": info["work_units"], "ctas": info["ctas"]},

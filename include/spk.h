@@ -399,11 +399,17 @@ spk_status spk_quantize_e4m3_rows(const float* X, int64_t M, int64_t K, int64_t 
 /* Many independent problems in one persistent launch.  Every item names a
  * pattern (with a balanced schedule attached), its values, dense operands and
  * output; op is 0 (SDDMM: out = FP32 nnz array) or 1 (SpMM: out = C, FP32).
- * Items may differ in size, K (1..512) and dtype (F32 or BF16, both operands
- * alike).  The run is a single kernel launch that pulls (item, chunk) work off
- * a device counter, so it can be captured in a CUDA graph and replayed; the
- * counter resets itself at the end of each run.  Pointers are fixed at
- * creation: replays read whatever the buffers hold at that time. */
+ * Items may differ in size, K (a whole number of 16-byte vectors, at most 16
+ * of them: K <= 64 in F32, <= 128 in BF16) and dtype (F32 or BF16, both
+ * operands alike).  The run is a single kernel launch that pulls (item, chunk)
+ * work off a device counter, so it can be captured in a CUDA graph and
+ * replayed; the counter resets itself at the end of each run.  Pointers are
+ * fixed at creation: replays read whatever the buffers hold at that time.
+ * Each item runs the shape its tune names (spk_batch_shapes lists them per
+ * op; default by K); every warp gets the largest shared-memory ring among the
+ * items' shapes, and a batch with an item of 8-nonzero batches or BF16
+ * operands runs the kernel build with 96 registers per thread (5 CTAs of 4
+ * warps per SM; else 80 registers, 6 CTAs). */
 typedef struct spk_batch_item {
     int32_t op;               /* 0 SDDMM, 1 SpMM                              */
     spk_csr S;
@@ -425,6 +431,15 @@ spk_status spk_batch_size(const spk_batch_item* items, int32_t count, size_t* by
 spk_status spk_batch_create(const spk_batch_item* items, int32_t count, void* storage,
                             size_t bytes, spk_batch* out, void* stream);
 spk_status spk_batch_run(spk_batch Bt, void* stream);
+/* The (group_lanes, vecs_per_lane, unroll) shapes batched items of op (0
+ * SDDMM, 1 SpMM) can run: writes min(count, capacity) triples to out (may be
+ * NULL), returns count (0 for another op). */
+int32_t spk_batch_shapes(int32_t op, int32_t* out, int32_t capacity);
+/* The kernel build later spk_batch_run calls use: regs = 80 (6 CTAs of 4
+ * warps per SM), 96 (5 CTAs) or 0 (the build spk_batch_create chose); the
+ * grid is recomputed.  Host only: runs already launched, and graphs captured
+ * earlier, keep the build they were given. */
+spk_status spk_batch_set_registers(spk_batch Bt, int32_t regs);
 /* Number of (item, chunk) work units and CTAs of one run. */
 spk_status spk_batch_info(spk_batch Bt, int64_t* work_units, int32_t* ctas);
 spk_status spk_batch_destroy(spk_batch Bt);

@@ -54,6 +54,8 @@ _PROTOS = {
     "spk_last_error": (ctypes.c_char_p, []),
     "spk_version": (_i32, []),
     "spk_shapes": (_i32, [_vp, _i32]),
+    "spk_batch_shapes": (_i32, [_i32, _vp, _i32]),
+    "spk_batch_set_registers": (ctypes.c_int, [_vp, _i32]),
     "spk_tune_default": (ctypes.c_int, [_vp, _i32, ctypes.c_int, _i32, _P(Tune)]),
     "spk_csr_create": (ctypes.c_int, [_P(_vp), _i64, _i64, _i64, _vp, _vp]),
     "spk_csr_destroy": (ctypes.c_int, [_vp]),
@@ -145,6 +147,15 @@ def check(status: int, where: str) -> None:
     if status != 0:
         msg = lib().spk_last_error()
         raise SpkError(status, where, msg.decode() if msg else "")
+
+
+def batch_shapes(op: int) -> list[tuple[int, int, int]]:
+    """(group_lanes, vecs_per_lane, unroll) shapes the batched launch offers
+    for op (0 SDDMM, 1 SpMM)."""
+    n = lib().spk_batch_shapes(op, None, 0)
+    buf = (ctypes.c_int32 * (3 * max(n, 1)))()
+    lib().spk_batch_shapes(op, buf, n)
+    return [(buf[3 * i], buf[3 * i + 1], buf[3 * i + 2]) for i in range(n)]
 
 
 def compiled_shapes() -> list[tuple[int, int, int]]:

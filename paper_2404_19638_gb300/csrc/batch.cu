@@ -25,33 +25,43 @@ struct BatchDesc {
     SpmmArgs sp;
 };
 
-// (G, NV, U) shapes available to batched items; class = dtype * 8 + position
-// in this list.  Each (op, class) routine is a separate non-inlined function,
-// so the merged kernel needs no more registers than its largest routine.
-#define SPK_BATCH_SHAPES(X) \
-    X(0, 4, 1, 4)           \
-    X(1, 8, 1, 4)           \
+// (G, NV, U) shapes available to batched items, per op; class = dtype * 8 +
+// position in the op's list.  Each (op, class) routine is a separate
+// non-inlined function, so the merged kernel needs no more registers than its
+// largest routine.
+#define SPK_BATCH_SDDMM_SHAPES(X) \
+    X(0, 4, 1, 4)                 \
+    X(1, 8, 1, 4)                 \
     X(2, 16, 1, 4)
+#define SPK_BATCH_SPMM_SHAPES(X) \
+    X(0, 4, 1, 4)                \
+    X(1, 8, 1, 4)                \
+    X(2, 16, 1, 4)               \
+    X(3, 4, 1, 8)                \
+    X(4, 8, 1, 8)                \
+    X(5, 16, 1, 8)
 
-constexpr int kBatchShapes = 3;
-static const Shape kBatchShapeList[kBatchShapes] = {
+constexpr int kBatchSddmmShapes = 3;
+constexpr int kBatchSpmmShapes = 6;
+static const Shape kBatchSddmmList[kBatchSddmmShapes] = {
 #define X(i, G_, NV_, U_) {G_, NV_, U_},
-    SPK_BATCH_SHAPES(X)
+    SPK_BATCH_SDDMM_SHAPES(X)
+#undef X
+};
+static const Shape kBatchSpmmList[kBatchSpmmShapes] = {
+#define X(i, G_, NV_, U_) {G_, NV_, U_},
+    SPK_BATCH_SPMM_SHAPES(X)
 #undef X
 };
 
 constexpr int kBatchThreads = 128;
 
-// Shared-memory ring of one warp: the largest ring of the batched shapes.
-__host__ __device__ constexpr int batch_ring_bytes()
+// Shared-memory ring of one warp for one (op, shape); a batch gives every warp
+// the largest ring among its items' shapes.
+static int batch_ring_bytes(int op, const Shape& sh)
 {
-    int m = 0;
-#define X(i, G_, NV_, U_)                                                           \
-    m = sddmm_ring_bytes(G_, NV_, U_, 2) > m ? sddmm_ring_bytes(G_, NV_, U_, 2) : m; \
-    m = spmm_ring_bytes(NV_, U_) > m ? spmm_ring_bytes(NV_, U_) : m;
-    SPK_BATCH_SHAPES(X)
-#undef X
-    return m;
+    const int b = op == 0 ? sddmm_ring_bytes(sh.G, sh.NV, sh.U, 2) : spmm_ring_bytes(sh.NV, sh.U);
+    return (b + 127) / 128 * 128;
 }
 
 // SDDMM: one chunk per warp (groups take interleaved batches of it), gathered
@@ -84,12 +94,16 @@ __device__ __noinline__ void batch_spmm_unit(const SpmmArgs& a, int64_t unit, in
         spmm_ring_span<DT, G, NV, U, false>(a, g, wring, kb, nkb, b0.x, b0.y, b1.x, b1.y, m, hs0);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
+// MINB: CTAs per SM the register budget is cut for (6: 80 registers; 5: 96
+// registers, for batches with 8-nonzero SpMM batches or BF16 operands, whose
+// routines would spill at 80).
+template <int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) k_batch(const BatchDesc* __restrict__ descs, int32_t count,
                                                   const int64_t* __restrict__ unit_begin, int64_t total_units,
-                                                  unsigned long long* counter, unsigned int* done)
+                                                  unsigned long long* counter, unsigned int* done, int32_t ring_bytes)
 {
     extern __shared__ __align__(16) unsigned char batch_smem[];
-    unsigned char* wsm = batch_smem + (threadIdx.x >> 5) * batch_ring_bytes();
+    unsigned char* wsm = batch_smem + (threadIdx.x >> 5) * ring_bytes;
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long u = 0;
@@ -109,7 +123,7 @@ __global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchDesc* __r
 #define X(i, G_, NV_, U_)                                                           \
     case i: batch_sddmm_unit<DT_F32, G_, NV_, U_>(d.sd, local, wsm); break;         \
     case 8 + i: batch_sddmm_unit<DT_BF16, G_, NV_, U_>(d.sd, local, wsm); break;
-                SPK_BATCH_SHAPES(X)
+                SPK_BATCH_SDDMM_SHAPES(X)
 #undef X
             }
         } else {
@@ -117,7 +131,7 @@ __global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchDesc* __r
 #define X(i, G_, NV_, U_)                                                           \
     case i: batch_spmm_unit<DT_F32, G_, NV_, U_>(d.sp, local, d.nkb, wsm); break;   \
     case 8 + i: batch_spmm_unit<DT_BF16, G_, NV_, U_>(d.sp, local, d.nkb, wsm); break;
-                SPK_BATCH_SHAPES(X)
+                SPK_BATCH_SPMM_SHAPES(X)
 #undef X
             }
         }
@@ -143,6 +157,9 @@ struct spk_batch_s {
     int32_t count;
     int64_t total_units;
     int32_t grid;
+    int32_t ring_bytes;              // per warp: the largest ring among the items' shapes
+    bool wide;                       // the 96-register kernel build (see plan_batch)
+    bool wide_default;               // the build plan_batch chose
     const BatchDesc* d_descs;
     const int64_t* d_unit_begin;
     unsigned long long* d_counter;
@@ -163,6 +180,8 @@ struct BatchPlan {
     std::vector<int64_t> unit_begin;
     size_t off_descs, off_units, off_counter, off_done, off_carry, total;
     std::vector<size_t> carry_off;   // per item (SpMM), relative to off_carry
+    int ring_bytes = 0;              // per warp
+    bool wide = false;               // some item batches 8 nonzeros or has BF16 operands
 };
 
 static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPlan& P)
@@ -214,11 +233,16 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
             if (it.tune->vecs_per_lane) NV = it.tune->vecs_per_lane;
             if (it.tune->unroll) U = it.tune->unroll;
         }
+        const Shape* list = it.op == 0 ? kBatchSddmmList : kBatchSpmmList;
+        const int nlist = it.op == 0 ? kBatchSddmmShapes : kBatchSpmmShapes;
         int sidx = -1;
-        for (int q = 0; q < kBatchShapes; ++q)
-            if (kBatchShapeList[q].G == G && kBatchShapeList[q].NV == NV && kBatchShapeList[q].U == U) sidx = q;
+        for (int q = 0; q < nlist; ++q)
+            if (list[q].G == G && list[q].NV == NV && list[q].U == U) sidx = q;
         if (sidx < 0 || G * NV < nvec)
             return bfail(SPK_ERR_UNSUPPORTED, where + "shape not available in batched mode");
+        const int rb = batch_ring_bytes(it.op, list[sidx]);
+        if (rb > P.ring_bytes) P.ring_bytes = rb;
+        if (list[sidx].U > 4 || it.dt == SPK_BF16) P.wide = true;
         BatchDesc& d = P.descs[m];
         d.op = it.op;
         d.cls = (it.dt == SPK_BF16 ? 8 : 0) + sidx;
@@ -263,6 +287,22 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
     return SPK_OK;
 }
 
+// One wave of CTAs of the chosen kernel build on the current device, with
+// 4 warps x ring_bytes of shared memory per CTA.
+static cudaError_t batch_grid(bool wide, int ring_bytes, int* grid)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)(kBatchThreads / 32) * ring_bytes;
+    const void* fn = wide ? (const void*)&k_batch<5> : (const void*)&k_batch<6>;
+    if (e == cudaSuccess && smem > 48 * 1024)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBatchThreads, smem);
+    *grid = sms * (per_sm > 0 ? per_sm : 1);
+    return e;
+}
+
 extern "C" spk_status spk_batch_size(const spk_batch_item* items, int32_t count, size_t* bytes)
 {
     if (!bytes) return bfail(SPK_ERR_ARG, "spk_batch_size: bytes is NULL");
@@ -296,17 +336,17 @@ extern "C" spk_status spk_batch_create(const spk_batch_item* items, int32_t coun
     if (e == cudaSuccess) e = cudaMemsetAsync(st + P.off_counter, 0, 512, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)(kBatchThreads / 32) * batch_ring_bytes();
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBatchThreads, smem);
+    int grid = 0;
+    e = batch_grid(P.wide, P.ring_bytes, &grid);
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_create: ") + cudaGetErrorString(e));
     spk_batch_s* B = new (std::nothrow) spk_batch_s();
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_create: out of host memory");
     B->count = count;
     B->total_units = P.unit_begin[count];
-    B->grid = sms * (per_sm > 0 ? per_sm : 1);
+    B->grid = grid;
+    B->ring_bytes = P.ring_bytes;
+    B->wide = P.wide;
+    B->wide_default = P.wide;
     B->d_descs = reinterpret_cast<const BatchDesc*>(st + P.off_descs);
     B->d_unit_begin = reinterpret_cast<const int64_t*>(st + P.off_units);
     B->d_counter = reinterpret_cast<unsigned long long*>(st + P.off_counter);
@@ -319,11 +359,44 @@ extern "C" spk_status spk_batch_run(spk_batch B, void* stream)
 {
     if (!B) return bfail(SPK_ERR_ARG, "spk_batch_run: handle is NULL");
     if (B->total_units == 0) return SPK_OK;
-    const size_t smem = (size_t)(kBatchThreads / 32) * batch_ring_bytes();
-    k_batch<<<B->grid, kBatchThreads, smem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin,
-                                                                   B->total_units, B->d_counter, B->d_done);
+    const size_t smem = (size_t)(kBatchThreads / 32) * B->ring_bytes;
+    if (B->wide)
+        k_batch<5><<<B->grid, kBatchThreads, smem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin,
+                                                                          B->total_units, B->d_counter, B->d_done,
+                                                                          B->ring_bytes);
+    else
+        k_batch<6><<<B->grid, kBatchThreads, smem, (cudaStream_t)stream>>>(B->d_descs, B->count, B->d_unit_begin,
+                                                                          B->total_units, B->d_counter, B->d_done,
+                                                                          B->ring_bytes);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_run: ") + cudaGetErrorString(e));
+    return SPK_OK;
+}
+
+extern "C" int32_t spk_batch_shapes(int32_t op, int32_t* out, int32_t capacity)
+{
+    if (op != 0 && op != 1) return 0;
+    const Shape* list = op == 0 ? kBatchSddmmList : kBatchSpmmList;
+    const int n = op == 0 ? kBatchSddmmShapes : kBatchSpmmShapes;
+    for (int i = 0; out && i < n && i < capacity; ++i) {
+        out[3 * i] = list[i].G;
+        out[3 * i + 1] = list[i].NV;
+        out[3 * i + 2] = list[i].U;
+    }
+    return n;
+}
+
+extern "C" spk_status spk_batch_set_registers(spk_batch B, int32_t regs)
+{
+    if (!B) return bfail(SPK_ERR_ARG, "spk_batch_set_registers: handle is NULL");
+    if (regs != 0 && regs != 80 && regs != 96)
+        return bfail(SPK_ERR_ARG, "spk_batch_set_registers: regs must be 0, 80 or 96");
+    const bool wide = regs == 0 ? B->wide_default : regs == 96;
+    int grid = 0;
+    cudaError_t e = batch_grid(wide, B->ring_bytes, &grid);
+    if (e != cudaSuccess) return bfail(SPK_ERR_CUDA, std::string("spk_batch_set_registers: ") + cudaGetErrorString(e));
+    B->wide = wide;
+    B->grid = grid;
     return SPK_OK;
 }
 

@@ -185,3 +185,90 @@ def test_batch_autotune_keeps_results(spk):
     for S, B, out, p in keep:
         ref = oracle.spmm(p.rowptr, p.colidx, p.B, p.vals)
         assert comp_err(out.cpu().numpy(), ref, oracle.spmm(p.rowptr, p.colidx, p.B, p.vals, absmode=True)) <= TOL
+
+
+def _batch_items(spk, probs, dt, W=128):
+    items, keep = [], []
+    for p in probs:
+        S = spk.CSR(p.rowptr, p.colidx, (p.M, p.N), torch.from_numpy(p.vals), device=DEV, chunk_work=W)
+        A = torch.from_numpy(p.A).to(DEV).to(dt)
+        B = torch.from_numpy(p.B).to(DEV).to(dt)
+        out = torch.full((p.nnz,), float("nan"), device=DEV)
+        C = torch.full((p.M, p.K), float("nan"), device=DEV)
+        items.append(spk.Item(spk.OP_SDDMM, S, B, out, A=A))
+        items.append(spk.Item(spk.OP_SPMM, S, B, C))
+        keep.append((S, A, B, out, C, p))
+    return items, keep
+
+
+def _check_batch_outputs(keep, dt):
+    for S, A, B, out, C, p in keep:
+        Aq = A.float().cpu().numpy(); Bq = B.float().cpu().numpy()
+        assert comp_err(out.cpu().numpy(), oracle.sddmm(p.rowptr, p.colidx, Aq, Bq, p.vals),
+                        oracle.sddmm(p.rowptr, p.colidx, Aq, Bq, p.vals, absmode=True)) <= TOL, p.name
+        assert comp_err(C.cpu().numpy(), oracle.spmm(p.rowptr, p.colidx, Bq, p.vals),
+                        oracle.spmm(p.rowptr, p.colidx, Bq, p.vals, absmode=True)) <= TOL, p.name
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+def test_batch_every_shape_and_register_budget(spk, dt):
+    """Every batched shape of each op (spk_batch_shapes) that fits K, under both
+    kernel builds (80 and 96 registers): results against the oracle, and bit
+    for bit equal to a standalone launch of the same shape and schedule where
+    that shape is compiled standalone."""
+    from paper_2404_19638_gb300.binding import batch_shapes, compiled_shapes
+    probs = _batch_problems(8, seed=31)
+    items, keep = _batch_items(spk, probs, dt)
+    batch = spk.Batch(items)
+    vecn = 4 if dt == torch.float32 else 8
+    standalone = set(compiled_shapes())
+    for op in (0, 1):
+        for shape in batch_shapes(op):
+            G, NV, U = shape
+            for k, it in enumerate(items):
+                nvec = it.B.size(1) // vecn
+                fit = it.op == op and G * NV >= nvec
+                batch.set_item_tune(k, {"group_lanes": G, "vecs_per_lane": NV, "unroll": U} if fit else None)
+            batch._create()
+            for regs in (80, 96):
+                batch.set_registers(regs)
+                for _, _, _, out, C, _ in keep:
+                    out.fill_(float("nan")); C.fill_(float("nan"))
+                batch.run()
+                torch.cuda.synchronize()
+                _check_batch_outputs(keep, dt)
+                if shape not in standalone:
+                    continue
+                tune = {"variant": 2, "group_lanes": G, "vecs_per_lane": NV, "unroll": U}
+                for S, A, B, out, C, p in keep:
+                    if G * NV < p.K // vecn:
+                        continue
+                    if op == 0:
+                        assert torch.equal(out, spk.sddmm(S, A, B, tune=tune)), (shape, p.name)
+                    else:
+                        assert torch.equal(C, spk.spmm(S, B, tune=tune)), (shape, p.name)
+            batch.set_registers(0)
+
+
+def test_batch_per_item_autotune(spk):
+    """Per-item tuning (chunk size per group of patterns, shape per class,
+    register budget): every choice is a valid one and the tuned launch still
+    matches the oracle, also after graph capture."""
+    from paper_2404_19638_gb300.binding import batch_shapes
+    probs = _batch_problems(10, seed=41, n_hi=6000)
+    items, keep = _batch_items(spk, probs, torch.float32, W=512)
+    batch = spk.Batch(items)
+    res = batch.autotune((128, 512), reps=1, per_item=True, min_gain=0.0)
+    assert res["chunk_work"] in (128, 512) and res["registers"] in ("default", 80, 96)
+    assert res["trials"] > 0 and res["ms_final"] <= min(res["ms"].values())
+    for name, shape in res["shapes"].items():
+        op = 0 if name.startswith("sddmm") else 1
+        assert shape is None or tuple(shape) in batch_shapes(op)
+    for S, *_ in keep:
+        assert S.schedule_info()["chunk_work"] in (64, 128, 256, 512, 1024)
+    batch.capture()
+    for _, _, _, out, C, _ in keep:
+        out.fill_(float("nan")); C.fill_(float("nan"))
+    batch.replay()
+    torch.cuda.synchronize()
+    _check_batch_outputs(keep, torch.float32)
