@@ -119,7 +119,8 @@ class Batch:
         each class of items of one op, K and dtype; the kernel's register
         budget (80 or 96).  Returns {"chunk_work": W, "ms": {W: ms}} plus,
         with per_item, "chunk_work_by_nnz", "shapes", "registers", "ms_final"
-        and "trials"."""
+        and "trials" (whole launches timed after the first stage, each
+        reps + 1 runs; the count depends only on the items and chunk_works)."""
         patterns = self._patterns()
         times = {}
         for W in chunk_works:
@@ -145,9 +146,7 @@ class Batch:
         chunk_by_group = {}
         for key in sorted(groups, reverse=True):
             chosen = best
-            for W in sorted(set(chunk_works) | {1024}):
-                if W == chosen:
-                    continue
+            for W in [w for w in sorted(set(chunk_works) | {1024}) if w != best]:
                 for S in groups[key]:
                     S.build_schedule(W)
                 self._create()

@@ -344,22 +344,30 @@ extern "C" spk_status spk_permute_values(const float* x, const int32_t* map, int
 // ----------------------------------------------------------------------------
 enum { OP_SDDMM = 0, OP_SPMM = 1, OP_SPMM_T = 2 };
 
-// Default lane-group shape for a row of nvec 16-byte vectors, 4 nonzeros in
-// flight per group (measured on R-MAT scale-20 rows with K = 64: SDDMM runs
-// best with 8 lanes per row and 2 vectors per lane, SpMM with one vector per
-// lane up to 16 lanes).
-// Defaults from shape sweeps on GB300 (R-MAT scale 20, K = 64): SDDMM
-// favours 4-lane groups with two vectors at 8 vectors a row and 8-lane groups
-// at 16; SpMM favours one vector a lane (16 lanes, 8 nonzeros in flight at
-// 16 vectors).
-static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16 = false)
+// Default lane-group shape for a row of nvec 16-byte vectors, from shape
+// sweeps on GB300 with the L2 flushed before each launch (R-MAT scale 20 and
+// 22 with K = 64, the K = 128 Chung-Lu pattern of 50M nonzeros):
+//   SDDMM: 4 lanes x 2 vectors at 8 vectors a row, 8 lanes x 2 vectors at 16,
+//          8 lanes x 4 vectors at 32, 4 nonzeros in flight;
+//   SpMM (and S^T Y): one vector a lane on 16 lanes with 8 nonzeros in
+//          flight at 16 vectors; 16 lanes x 2 vectors x 8 at 32 (rec FP32
+//          1.90 ms against 2.24 for 8 x 4 x 4).  16-bit rows of 8 vectors
+//          spread over 16 lanes as 8-byte vectors (8 nonzeros in flight) when
+//          rows are long (rmat20, 15 nonzeros a row: 0.412 ms), else 8 lanes
+//          of 16-byte vectors with 4 in flight (R-MAT scale 22, 8 a row:
+//          0.803 ms against 0.867); 16-bit rows of 16 vectors take 8 lanes x
+//          2 vectors x 4 (rec BF16 1.26 ms against 1.58 for 32 lanes of
+//          8-byte vectors).
+static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16 = false, bool short_rows = false)
 {
     *U = 4;
     if (op != OP_SDDMM && half16) {
-        // 16-bit SpMM: 8-byte lane vectors over twice the lanes
-        if (nvec <= 4) { *G = 8; *NV = 1; return; }
-        if (nvec <= 8) { *G = 16; *NV = 1; *U = 8; return; }
-        if (nvec <= 16) { *G = 32; *NV = 1; *U = 8; return; }
+        if (nvec <= 4) { *G = 8; *NV = 1; return; }                 // 8-byte vectors over 8 lanes
+        if (nvec <= 8) {
+            if (short_rows) { *G = 8; *NV = 1; return; }              // 16-byte vectors
+            *G = 16; *NV = 1; *U = 8; return;                        // 8-byte vectors
+        }
+        if (nvec <= 16) { *G = 8; *NV = 2; return; }                 // 16-byte vectors
     }
     if (nvec <= 4) { *G = 4; *NV = 1; }
     else if (nvec <= 8) { *G = (op == OP_SDDMM) ? 4 : 8; *NV = (op == OP_SDDMM) ? 2 : 1; }
@@ -368,7 +376,11 @@ static void default_shape(int op, int nvec, int* G, int* NV, int* U, bool half16
         *NV = (op == OP_SDDMM) ? 2 : 1;
         *U = (op == OP_SDDMM) ? 4 : 8;
     }
-    else if (nvec <= 32) { *G = 8; *NV = 4; }
+    else if (nvec <= 32) {
+        *G = (op == OP_SDDMM) ? 8 : 16;
+        *NV = (op == OP_SDDMM) ? 4 : 2;
+        *U = (op == OP_SDDMM) ? 4 : 8;
+    }
     else if (nvec <= 64) { *G = 32; *NV = 2; }
     else { *G = 32; *NV = 4; }
 }
@@ -382,7 +394,8 @@ static spk_status resolve(const spk_csr_s* S, int op, int dtb, int K, bool vec, 
     const int nvec = K / vecn;
     int G, NV, U;
     const bool half16 = vec && (variant == 2) && (dtb == SPK_BF16 || dtb == SPK_F16) && K % 4 == 0;
-    default_shape(op, nvec, &G, &NV, &U, half16);
+    const bool short_rows = S->M > 0 && S->nnz < 12 * S->M;            // fewer than 12 nonzeros a row
+    default_shape(op, nvec, &G, &NV, &U, half16, short_rows);
     if (t && t->group_lanes) G = t->group_lanes;
     if (t && t->vecs_per_lane) NV = t->vecs_per_lane;
     if (t && t->unroll) U = t->unroll;

@@ -303,3 +303,37 @@ def test_spmm_16bit_lane_layouts(spk, dt, K):
         got = spk.spmm(S, tB, tune={"variant": 2, "group_lanes": G, "vecs_per_lane": NV, "unroll": U}).cpu().numpy()
         assert np.array_equal(got, base), shape
     assert np.array_equal(spk.spmm(S, tB).cpu().numpy(), base)
+
+
+def test_default_shapes_by_row_length(spk):
+    """The library's default SpMM shape depends on K, the dtype and, for
+    16-bit rows of 8 vectors, on whether rows average fewer than 12 nonzeros;
+    every default runs and matches the oracle (and the register path bit for
+    bit) on a short-row and a long-row pattern."""
+    M, N = 600, 500
+    g = np.random.default_rng(77)
+    short = synth.csr_from_coo(np.repeat(np.arange(M), 4), g.integers(0, N, 4 * M), M, N)
+    long_ = synth.csr_from_coo(np.repeat(np.arange(M), 20), g.integers(0, N, 20 * M), M, N)
+    want = {  # (pattern, dtype code, K) -> default SpMM shape
+        ("short", 1, 64): (8, 1, 4), ("long", 1, 64): (16, 1, 8),
+        ("short", 1, 128): (8, 2, 4), ("long", 1, 128): (8, 2, 4),
+        ("short", 0, 128): (16, 2, 8), ("long", 0, 64): (16, 1, 8),
+    }
+    for (name, code, K), shape in want.items():
+        rp, ci = short if name == "short" else long_
+        vals = g.uniform(-1, 1, ci.size).astype(np.float32)
+        S = spk.CSR(rp, ci, (M, N), torch.from_numpy(vals), device=DEV)
+        t = S.tune_default(1, code, K)
+        assert (t["group_lanes"], t["vecs_per_lane"], t["unroll"]) == shape, (name, code, K, t)
+        Bf = g.standard_normal((N, K)).astype(np.float32)
+        tB = torch.from_numpy(Bf).to(DEV)
+        if code == 1:
+            tB = spk.cast(tB, torch.bfloat16)
+            Bq = tB.view(torch.int16).cpu().numpy().view(np.uint16)
+            fmt = "bf16"
+        else:
+            Bq, fmt = Bf, None
+        got = spk.spmm(S, tB).cpu().numpy()
+        assert comp_err(got, oracle.spmm(rp, ci, Bq, vals, fmt_b=fmt),
+                        oracle.spmm(rp, ci, Bq, vals, fmt_b=fmt, absmode=True)) <= TOL, (name, code, K)
+        assert np.array_equal(got, spk.spmm(S, tB, tune={"variant": 3}).cpu().numpy()), (name, code, K)
