@@ -625,6 +625,11 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     else if (nvh <= 16) G = 16;
     else if (nvh <= 32) { G = 32; U = 8; }
     else { G = 32; NV = 2; }
+    // one FP32 head of 16 vectors: 8 lanes x 2 vectors (rmat20, K = 64:
+    // 0.85 ms against 1.16 for the all-heads kernel's 16 lanes x 1 vector;
+    // 16-bit rows spill at this shape)
+    const bool f32_head16 = dt == SPK_F32 && heads == 1 && nvh == 16;
+    if (f32_head16) { G = 8; NV = 2; }
     if (tune && tune->group_lanes) G = tune->group_lanes;
     if (tune && tune->vecs_per_lane) NV = tune->vecs_per_lane;
     if (tune && tune->unroll) U = tune->unroll;
@@ -652,7 +657,8 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     // heads split the group evenly (unless a shape was asked for)
     const int nv = K / vecn;
     const bool shaped = tune && (tune->group_lanes || tune->vecs_per_lane || tune->unroll);
-    const bool mh = !shaped && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 && nv / heads >= 1;
+    const bool mh = !shaped && !f32_head16 && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 &&
+                    nv / heads >= 1;
     cudaError_t e;
     if (mh) {
         e = launch_fused_mh(dt, nv, a, (cudaStream_t)stream);

@@ -26,9 +26,10 @@ namespace spk {
     X(1, 8, 1, 4)           \
     X(2, 16, 1, 4)          \
     X(3, 32, 1, 8)          \
-    X(4, 32, 2, 4)
+    X(4, 32, 2, 4)          \
+    X(5, 8, 2, 4)
 
-constexpr int kFusedShapes = 5;
+constexpr int kFusedShapes = 6;
 static const Shape kFusedShapeList[kFusedShapes] = {
 #define X(i, G_, NV_, U_) {G_, NV_, U_},
     SPK_FUSED_SHAPES(X)
