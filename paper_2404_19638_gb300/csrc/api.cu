@@ -625,11 +625,13 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     else if (nvh <= 16) G = 16;
     else if (nvh <= 32) { G = 32; U = 8; }
     else { G = 32; NV = 2; }
-    // one FP32 head of 16 vectors: 8 lanes x 2 vectors (rmat20, K = 64:
-    // 0.85 ms against 1.16 for the all-heads kernel's 16 lanes x 1 vector;
-    // 16-bit rows spill at this shape)
-    const bool f32_head16 = dt == SPK_F32 && heads == 1 && nvh == 16;
-    if (f32_head16) { G = 8; NV = 2; }
+    // One head of K = 64 (rmat20, GB300): FP32 rows of 16 vectors on 8 lanes x
+    // 2 vectors, 0.85 ms against 1.16 for the all-heads kernel's 16 lanes;
+    // 16-bit rows of 8 vectors on the one-head kernel's 8 lanes, 0.86 ms
+    // against 1.24 for the all-heads kernel at the same width.
+    const bool one_head = heads == 1 && ((dt == SPK_F32 && nvh == 16) || (dt != SPK_F32 && nvh == 8));
+    if (one_head && dt == SPK_F32) { G = 8; NV = 2; }
+    if (one_head && dt != SPK_F32) { G = 8; NV = 1; }
     if (tune && tune->group_lanes) G = tune->group_lanes;
     if (tune && tune->vecs_per_lane) NV = tune->vecs_per_lane;
     if (tune && tune->unroll) U = tune->unroll;
@@ -657,7 +659,7 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     // heads split the group evenly (unless a shape was asked for)
     const int nv = K / vecn;
     const bool shaped = tune && (tune->group_lanes || tune->vecs_per_lane || tune->unroll);
-    const bool mh = !shaped && !f32_head16 && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 &&
+    const bool mh = !shaped && !one_head && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 &&
                     nv / heads >= 1;
     cudaError_t e;
     if (mh) {

@@ -27,9 +27,10 @@ namespace spk {
     X(2, 16, 1, 4)          \
     X(3, 32, 1, 8)          \
     X(4, 32, 2, 4)          \
-    X(5, 8, 2, 4)
+    X(5, 8, 2, 4)           \
+    X(6, 4, 2, 4)
 
-constexpr int kFusedShapes = 6;
+constexpr int kFusedShapes = 7;
 static const Shape kFusedShapeList[kFusedShapes] = {
 #define X(i, G_, NV_, U_) {G_, NV_, U_},
     SPK_FUSED_SHAPES(X)
@@ -424,9 +425,18 @@ __device__ __forceinline__ void fused_span(const FusedArgs& a, const Group<G>& g
     for (int rr = cur + 1; rr <= meta.z; ++rr) fused_zero_row<VECN, G, NV>(a, g, kb, nvh, rr);
 }
 
+// CTAs per SM the register budget is cut for: as many as shared memory
+// allows, at most 8 (128 registers); 16-bit rows of two vectors a lane keep
+// twice the widened elements and get 6 (168 registers) so that they do not spill.
+template <int DT, int NV, int U>
+constexpr int fused_min_ctas()
+{
+    return (DT != DT_F32 && NV > 1) ? 6
+                                    : (ring_min_ctas(fused_ring_bytes(NV, U)) < 8 ? ring_min_ctas(fused_ring_bytes(NV, U)) : 8);
+}
+
 template <int DT, int G, int NV, int U>
-__global__ void __launch_bounds__(RING_THREADS, ring_min_ctas(fused_ring_bytes(NV, U)) < 8 ? ring_min_ctas(fused_ring_bytes(NV, U)) : 8)
-    k_fused(const FusedArgs a)
+__global__ void __launch_bounds__(RING_THREADS, fused_min_ctas<DT, NV, U>()) k_fused(const FusedArgs a)
 {
     extern __shared__ __align__(16) unsigned char ring_smem[];
     const Group<G> g;

@@ -74,7 +74,7 @@ def test_fused_f32(spk, K, heads, softmax):
     _check(spk, rp, ci, vals, A, B, heads, softmax, torch.float32, W=128, seed_note=f"K={K} H={heads}")
 
 
-@pytest.mark.parametrize("shape", [(4, 1, 4), (8, 1, 4), (16, 1, 4), (32, 1, 8), (32, 2, 4), (8, 2, 4)])
+@pytest.mark.parametrize("shape", [(4, 1, 4), (8, 1, 4), (16, 1, 4), (32, 1, 8), (32, 2, 4), (8, 2, 4), (4, 2, 4)])
 def test_fused_head_per_grid_row(spk, shape):
     """The kernel with one head per grid row (used for rows of more than 32
     vectors, or when a shape is asked for)."""
