@@ -275,7 +275,10 @@ spk_status spk_spmm_static(spk_csr S, const float* vals, const float* vals2,
  * row is 0).  Needs the balanced schedule; workspace >=
  * spk_fusedmm_workspace_size bytes (16-byte aligned; NULL if that is 0).
  * Split rows are merged in a fixed order: results are deterministic.  Calls
- * that share one schedule must not overlap on the device. */
+ * that share one schedule must not overlap on the device.  tune: NULL (the
+ * library picks the kernel), group_lanes / vecs_per_lane / unroll for the
+ * one-head-per-grid-row kernel of that shape, or vecs_per_lane alone (1 or
+ * 2) for the all-heads kernel with that many adjacent vectors a lane. */
 spk_status spk_fusedmm_workspace_size(spk_csr S, int32_t K, int32_t heads, size_t* bytes);
 spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int32_t softmax, spk_dtype dt,
                        const void* A, int64_t lda, const void* B, int64_t ldb, int32_t K, int32_t heads,

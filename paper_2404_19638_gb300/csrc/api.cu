@@ -8,6 +8,7 @@
 #include <string>
 
 #include "common.cuh"
+#include "fused.cuh"
 
 namespace spk {
 
@@ -619,27 +620,52 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
             SPK_ERR_SHAPE, "spk_fusedmm: A, B, Y must be 16-byte aligned with 16-byte row strides");
     REQUIRE(!vals || aligned16(vals), SPK_ERR_ARG, "spk_fusedmm: vals must be 16-byte aligned");
     const int nvh = dh / vecn;
-    int G, NV = 1, U = 4;
-    if (nvh <= 4) G = 4;
-    else if (nvh <= 8) G = 8;
-    else if (nvh <= 16) G = 16;
-    else if (nvh <= 32) { G = 32; U = 8; }
-    else { G = 32; NV = 2; }
-    // One head of K = 64 (rmat20, GB300): FP32 rows of 16 vectors on 8 lanes x
-    // 2 vectors, 0.85 ms against 1.16 for the all-heads kernel's 16 lanes;
-    // 16-bit rows of 8 vectors on the one-head kernel's 8 lanes, 0.86 ms
-    // against 1.24 for the all-heads kernel at the same width.
+    const int nv = K / vecn;
+    // Kernel choice.  The all-heads kernel (one lane group per row, heads as
+    // blocks of G / heads lanes, NV adjacent vectors a lane) when a row is at
+    // most 32 vectors and the heads split the lanes evenly; else, or when a
+    // shape is asked for, the one-head-per-grid-row kernel.  Measured on
+    // rmat20, K = 64, GB300: one head runs best on the one-head kernel (FP32
+    // 8 lanes x 2 vectors 0.85 ms, 16-bit 8 lanes 0.86 ms, against 1.16 / 1.24
+    // on the all-heads kernel); 16-bit rows with 4 or more heads on the
+    // all-heads kernel with 2 vectors a lane (1.21 ms against 1.32).
+    // tune.vecs_per_lane alone (no group_lanes, no unroll) asks for the
+    // all-heads kernel with that many vectors a lane (1 or 2).
+    const bool mh_asked = tune && tune->vecs_per_lane && !tune->group_lanes && !tune->unroll;
+    const bool shaped = tune && (tune->group_lanes || tune->unroll || (tune->vecs_per_lane && !mh_asked));
     const bool one_head = heads == 1 && ((dt == SPK_F32 && nvh == 16) || (dt != SPK_F32 && nvh == 8));
-    if (one_head && dt == SPK_F32) { G = 8; NV = 2; }
-    if (one_head && dt != SPK_F32) { G = 8; NV = 1; }
-    if (tune && tune->group_lanes) G = tune->group_lanes;
-    if (tune && tune->vecs_per_lane) NV = tune->vecs_per_lane;
-    if (tune && tune->unroll) U = tune->unroll;
-    const int idx = fused_shape_index(G, NV, U);
-    REQUIRE(idx >= 0, SPK_ERR_UNSUPPORTED, "spk_fusedmm: no kernel for group_lanes=%d vecs_per_lane=%d unroll=%d", G,
-            NV, U);
-    REQUIRE(G * NV >= nvh, SPK_ERR_UNSUPPORTED, "spk_fusedmm: a group of %d x %d vectors cannot hold a head of %d",
-            G, NV, nvh);
+    auto mh_fits = [&](int nvl) {
+        const int g = nv / nvl;
+        return nv % nvl == 0 && (g == 4 || g == 8 || g == 16 || (g == 32 && nvl == 1)) && g % heads == 0;
+    };
+    int mh_nv = 1;
+    if (mh_asked) {
+        mh_nv = tune->vecs_per_lane;
+        REQUIRE(mh_nv == 1 || mh_nv == 2, SPK_ERR_ARG, "spk_fusedmm: vecs_per_lane must be 1 or 2 for the all-heads kernel");
+        REQUIRE(mh_fits(mh_nv), SPK_ERR_UNSUPPORTED,
+                "spk_fusedmm: %d vectors a row do not split into %d heads of %d-vector lanes", nv, heads, mh_nv);
+    } else if (dt != SPK_F32 && heads >= 4 && mh_fits(2)) {
+        mh_nv = 2;
+    }
+    const bool mh = mh_asked || (!shaped && !one_head && mh_fits(mh_nv));
+    int G, NV = 1, U = 4, idx = -1;
+    if (!mh) {
+        if (nvh <= 4) G = 4;
+        else if (nvh <= 8) G = 8;
+        else if (nvh <= 16) G = 16;
+        else if (nvh <= 32) { G = 32; U = 8; }
+        else { G = 32; NV = 2; }
+        if (one_head && dt == SPK_F32) { G = 8; NV = 2; }
+        if (one_head && dt != SPK_F32) { G = 8; NV = 1; }
+        if (tune && tune->group_lanes) G = tune->group_lanes;
+        if (tune && tune->vecs_per_lane) NV = tune->vecs_per_lane;
+        if (tune && tune->unroll) U = tune->unroll;
+        idx = fused_shape_index(G, NV, U);
+        REQUIRE(idx >= 0, SPK_ERR_UNSUPPORTED, "spk_fusedmm: no kernel for group_lanes=%d vecs_per_lane=%d unroll=%d",
+                G, NV, U);
+        REQUIRE(G * NV >= nvh, SPK_ERR_UNSUPPORTED, "spk_fusedmm: a group of %d x %d vectors cannot hold a head of %d",
+                G, NV, nvh);
+    }
     const size_t need = (size_t)S->npieces * (((size_t)K + 2 * (size_t)heads + 3) / 4 * 4) * 4;
     if (need > 0) {
         REQUIRE(workspace && ws_bytes >= need, SPK_ERR_WORKSPACE, "spk_fusedmm: workspace has %zu bytes, needs %zu",
@@ -655,15 +681,9 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     a.bnd = S->bnd; a.meta = S->meta; a.head_s0 = S->head_s0; a.slot_np = S->slot_np; a.cnt = S->cnt;
     a.carry = reinterpret_cast<float*>(workspace);
     a.nchunks = S->nchunks;
-    // all heads in one lane group when a row is at most 32 vectors and the
-    // heads split the group evenly (unless a shape was asked for)
-    const int nv = K / vecn;
-    const bool shaped = tune && (tune->group_lanes || tune->vecs_per_lane || tune->unroll);
-    const bool mh = !shaped && !one_head && (nv == 4 || nv == 8 || nv == 16 || nv == 32) && nv % heads == 0 &&
-                    nv / heads >= 1;
     cudaError_t e;
     if (mh) {
-        e = launch_fused_mh(dt, nv, a, (cudaStream_t)stream);
+        e = launch_fused_mh_nv(dt, nv / mh_nv, mh_nv, a, (cudaStream_t)stream);
     } else {
         Launch L;
         L.shape = idx; L.vec = true; L.threads = 64; L.chunks = true; L.ring = true; L.stages = 2;

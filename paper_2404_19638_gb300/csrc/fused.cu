@@ -17,6 +17,7 @@
 // (acc, m, l) of each piece in its carry slot; the last piece to arrive merges
 // them in slot order (log-sum-exp) and writes the row, so results do not
 // depend on scheduling.
+#include "fused.cuh"
 #include "ring.cuh"
 
 namespace spk {
@@ -557,11 +558,12 @@ __device__ __forceinline__ void mh_finish_piece(const FusedArgs& a, const Group<
     if (g.gl == 0) atomicExch(a.cnt + s0, 0);
 }
 
-template <int DT, int G, int U>
+template <int DT, int G, int U, int NV>
 __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>& g, uint4* wring, int r0, int e0,
                                               int r1, int e1, const int4 meta, int head_s0)
 {
     constexpr int VECN = vec_elems(DT);
+    constexpr int W = NV * VECN;                    // elements a lane holds: NV adjacent 16-byte vectors
     constexpr int TG = 4 * G;
     static_assert(U % 4 == 0 && TG % U == 0 && TG / U >= 2 && U <= G, "batches must tile the group tile");
     const int gl = g.gl;
@@ -570,41 +572,46 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
     const int NH = G / a.heads;                     // lanes per head
     const int hl = gl / NH;                         // this lane's head
     const bool hlead = (gl % NH) == 0;
-    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + gl * 16;
-    const char* __restrict__ Ab = reinterpret_cast<const char*>(a.A) + gl * 16;
+    const char* __restrict__ Bb = reinterpret_cast<const char*>(a.B) + gl * 16 * NV;
+    const char* __restrict__ Ab = reinterpret_cast<const char*>(a.A) + gl * 16 * NV;
     const unsigned ldb_bytes = (unsigned)a.ldb * dt_bytes(DT);
     const unsigned lda_bytes = (unsigned)a.lda * dt_bytes(DT);
     const float* __restrict__ vals = a.vals;
-    int* trow = reinterpret_cast<int*>(wring + 2 * U * 32) + grp * TG;
-    float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wring + 2 * U * 32) + 2 * 128) + grp * TG;
-    uint4* ringA = reinterpret_cast<uint4*>(reinterpret_cast<int*>(wring + 2 * U * 32) + 4 * 128);
+    int* trow = reinterpret_cast<int*>(wring + 2 * U * NV * 32) + grp * TG;
+    float* tval = reinterpret_cast<float*>(reinterpret_cast<int*>(wring + 2 * U * NV * 32) + 2 * 128) + grp * TG;
+    uint4* ringA = reinterpret_cast<uint4*>(reinterpret_cast<int*>(wring + 2 * U * NV * 32) + 4 * 128);
     const float scale = a.scale;
     const bool smax = a.softmax != 0;
 
-    float acc[VECN], av[VECN];
+    float acc[W], av[W];
 #pragma unroll
-    for (int q = 0; q < VECN; ++q) { acc[q] = 0.f; av[q] = 0.f; }
+    for (int q = 0; q < W; ++q) { acc[q] = 0.f; av[q] = 0.f; }
     float m = -INFINITY, l = 0.f;
     int cur = r0, acur = -1;
     auto flush = [&](int row) {
-        if (row == r0 && meta.x >= 0) mh_finish_piece<VECN, G>(a, g, hl, hlead, meta.x, head_s0, row, acc, m, l);
-        else if (row == r1 && meta.y >= 0) mh_finish_piece<VECN, G>(a, g, hl, hlead, meta.y, meta.y, row, acc, m, l);
-        else mh_write_row<VECN, G>(a, g, hl, hlead, row, acc, m, l);
+        if (row == r0 && meta.x >= 0) mh_finish_piece<W, G>(a, g, hl, hlead, meta.x, head_s0, row, acc, m, l);
+        else if (row == r1 && meta.y >= 0) mh_finish_piece<W, G>(a, g, hl, hlead, meta.y, meta.y, row, acc, m, l);
+        else mh_write_row<W, G>(a, g, hl, hlead, row, acc, m, l);
     };
     auto zero_out = [&](int row) {
-        float z[VECN];
+        float z[W];
 #pragma unroll
-        for (int q = 0; q < VECN; ++q) z[q] = 0.f;
-        mh_write_row<VECN, G>(a, g, hl, hlead, row, z, -INFINITY, 0.f);
+        for (int q = 0; q < W; ++q) z[q] = 0.f;
+        mh_write_row<W, G>(a, g, hl, hlead, row, z, -INFINITY, 0.f);
     };
-    auto unpack_v = [&](const uint4 v, float (&f)[VECN]) {
-        Raw<DT, VECN> r;
-        r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
-        unpack_all<DT, VECN>(r, f);
+    // the lane's NV vectors, 32 slots apart in the ring, widened to FP32
+    auto unpack_v = [&](const uint4* v, float (&f)[W]) {
+        Raw<DT, W> r;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const uint4 x = v[t * 32];
+            r.w[4 * t] = x.x; r.w[4 * t + 1] = x.y; r.w[4 * t + 2] = x.z; r.w[4 * t + 3] = x.w;
+        }
+        unpack_all<DT, W>(r, f);
     };
-    auto dot = [&](const float (&bf)[VECN]) {
+    auto dot = [&](const float (&bf)[W]) {
         float2 d2 = make_float2(0.f, 0.f);
-        dot_pairs<VECN>(d2, av, bf);
+        dot_pairs<W>(d2, av, bf);
         return d2.x + d2.y;
     };
 
@@ -661,16 +668,21 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                     rws[4 * c + 3] = __shfl_sync(g.mask, tr.w, src0 + c, G);
                 }
                 const int eb = tb0 + b * U;
-                uint4* sl = wring + (b & 1) * U * 32 + lane;
+                uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
                 bool copied = false;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (eb + u < e0 || eb + u >= e1) continue;
-                    cpa16(sl + u * 32, Bb + (size_t)(unsigned)j[u] * ldb_bytes);
+#pragma unroll
+                    for (int t = 0; t < NV; ++t)
+                        cpa16(sl + (u * NV + t) * 32, Bb + (size_t)(unsigned)j[u] * ldb_bytes + t * 16);
                     if (rws[u] != ilast) {
                         if (!copied) {
                             copied = true;
-                            cpa16(ringA + (b & 1) * 32 + lane, Ab + (size_t)(unsigned)rws[u] * lda_bytes);
+#pragma unroll
+                            for (int t = 0; t < NV; ++t)
+                                cpa16(ringA + ((b & 1) * NV + t) * 32 + lane,
+                                      Ab + (size_t)(unsigned)rws[u] * lda_bytes + t * 16);
                         }
                         ilast = rws[u];
                     }
@@ -686,7 +698,7 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
             cp_async_wait<1>();
             __syncwarp(g.mask);
             const int eb = tb0 + b * U;
-            const uint4* sl = wring + (b & 1) * U * 32 + lane;
+            const uint4* sl = wring + (b & 1) * U * NV * 32 + lane;
             const int o = (((b * U) / TG) & 1) * 128 + (b * U) % TG;
             int rc[U];
             float sc[U];
@@ -705,8 +717,8 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
             if (eb >= e0 && eb + U <= e1 && rc[U - 1] == cur && cur == acur) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    float bf[VECN];
-                    unpack_v(sl[u * 32], bf);
+                    float bf[W];
+                    unpack_v(sl + u * NV * 32, bf);
                     ev[u] = dot(bf);
                 }
                 head_allreduce<G, U>(g, NH, ev);
@@ -718,23 +730,23 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                     for (int u = 0; u < U; ++u) mb = fmaxf(mb, ev[u]);
                     const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
 #pragma unroll
-                    for (int q = 0; q < VECN; ++q) acc[q] *= c;
+                    for (int q = 0; q < W; ++q) acc[q] *= c;
                     l *= c;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const float w = expf(ev[u] - mb);
                         l += w;
-                        float bf[VECN];
-                        unpack_v(sl[u * 32], bf);           // re-read: keeps U rows out of registers
-                        axpy_pairs<VECN>(acc, w, bf);
+                        float bf[W];
+                        unpack_v(sl + u * NV * 32, bf);     // re-read: keeps U rows out of registers
+                        axpy_pairs<W>(acc, w, bf);
                     }
                     m = mb;
                 } else {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        float bf[VECN];
-                        unpack_v(sl[u * 32], bf);
-                        axpy_pairs<VECN>(acc, ev[u], bf);
+                        float bf[W];
+                        unpack_v(sl + u * NV * 32, bf);
+                        axpy_pairs<W>(acc, ev[u], bf);
                     }
                 }
             } else {
@@ -747,12 +759,12 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                     ev[u] = 0.f;
                     const int e = eb + u;
                     if (e < e0 || e >= e1) continue;
-                    float bfu[VECN];
-                    unpack_v(sl[u * 32], bfu);
+                    float bfu[W];
+                    unpack_v(sl + u * NV * 32, bfu);
                     if (rc[u] != acur) {
-                        if (first) unpack_v(ringA[(b & 1) * 32 + lane], av);
-                        else load_elems<DT, VECN>(reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)rc[u] * lda_bytes,
-                                                  (int64_t)gl * VECN, av);
+                        if (first) unpack_v(ringA + (b & 1) * NV * 32 + lane, av);
+                        else load_elems<DT, W>(reinterpret_cast<const char*>(a.A) + (size_t)(unsigned)rc[u] * lda_bytes,
+                                               (int64_t)gl * W, av);
                         first = false;
                         acur = rc[u];
                     }
@@ -769,23 +781,23 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
                         for (int rr = cur + 1; rr < rc[u]; ++rr) zero_out(rr);
                         cur = rc[u];
 #pragma unroll
-                        for (int q = 0; q < VECN; ++q) acc[q] = 0.f;
+                        for (int q = 0; q < W; ++q) acc[q] = 0.f;
                         m = -INFINITY;
                         l = 0.f;
                     }
-                    float bf[VECN];
-                    unpack_v(sl[u * 32], bf);
+                    float bf[W];
+                    unpack_v(sl + u * NV * 32, bf);
                     if (smax) {
                         const float mb = fmaxf(m, ev[u]);
                         const float c = (m == -INFINITY) ? 0.f : expf(m - mb);
 #pragma unroll
-                        for (int q = 0; q < VECN; ++q) acc[q] *= c;
+                        for (int q = 0; q < W; ++q) acc[q] *= c;
                         const float w = expf(ev[u] - mb);
                         l = l * c + w;
-                        axpy_pairs<VECN>(acc, w, bf);
+                        axpy_pairs<W>(acc, w, bf);
                         m = mb;
                     } else {
-                        axpy_pairs<VECN>(acc, ev[u], bf);
+                        axpy_pairs<W>(acc, ev[u], bf);
                     }
                 }
             }
@@ -804,14 +816,14 @@ __device__ __forceinline__ void fused_span_mh(const FusedArgs& a, const Group<G>
     for (int rr = cur + 1; rr <= meta.z; ++rr) zero_out(rr);
 }
 
-__host__ __device__ constexpr int fused_mh_ring_bytes(int U) { return fused_ring_bytes(1, U); }
+__host__ __device__ constexpr int fused_mh_ring_bytes(int U, int NV) { return fused_ring_bytes(NV, U); }
 
-template <int DT, int G, int U>
-__global__ void __launch_bounds__(RING_THREADS, DT == DT_F32 ? 8 : 6) k_fused_mh(const FusedArgs a)
+template <int DT, int G, int U, int NV>
+__global__ void __launch_bounds__(RING_THREADS, (DT == DT_F32 && NV == 1) ? 8 : 6) k_fused_mh(const FusedArgs a)
 {
     extern __shared__ __align__(16) unsigned char ring_smem[];
     const Group<G> g;
-    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (fused_mh_ring_bytes(U) / 16);
+    uint4* wring = reinterpret_cast<uint4*>(ring_smem) + (threadIdx.x >> 5) * (fused_mh_ring_bytes(U, NV) / 16);
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     for (int64_t c = gid; c < a.nchunks; c += ngroups) {
@@ -819,40 +831,53 @@ __global__ void __launch_bounds__(RING_THREADS, DT == DT_F32 ? 8 : 6) k_fused_mh
         const int4 m = a.meta[c];
         if (b1.y == b0.y && m.z < b0.x) continue;
         const int hs0 = (m.x >= 0) ? __ldg(a.head_s0 + c) : -1;
-        fused_span_mh<DT, G, U>(a, g, wring, b0.x, b0.y, b1.x, b1.y, m, hs0);
+        fused_span_mh<DT, G, U, NV>(a, g, wring, b0.x, b0.y, b1.x, b1.y, m, hs0);
     }
 }
 
 template <int DT>
-static cudaError_t launch_fused_mh_t(int G, const FusedArgs& a, cudaStream_t s)
+static cudaError_t launch_fused_mh_t(int G, int NV, const FusedArgs& a, cudaStream_t s)
 {
     const void* fn = nullptr;
-    switch (G) {
     // 4 nonzeros a batch (8 measured slower: more registers, fewer warps)
-    case 4: fn = (const void*)&k_fused_mh<DT, 4, 4>; break;
-    case 8: fn = (const void*)&k_fused_mh<DT, 8, 4>; break;
-    case 16: fn = (const void*)&k_fused_mh<DT, 16, 4>; break;
-    case 32: fn = (const void*)&k_fused_mh<DT, 32, 4>; break;
-    default: return cudaErrorInvalidValue;
+    if (NV == 1) {
+        switch (G) {
+        case 4: fn = (const void*)&k_fused_mh<DT, 4, 4, 1>; break;
+        case 8: fn = (const void*)&k_fused_mh<DT, 8, 4, 1>; break;
+        case 16: fn = (const void*)&k_fused_mh<DT, 16, 4, 1>; break;
+        case 32: fn = (const void*)&k_fused_mh<DT, 32, 4, 1>; break;
+        }
+    } else if (NV == 2) {
+        switch (G) {
+        case 4: fn = (const void*)&k_fused_mh<DT, 4, 4, 2>; break;
+        case 8: fn = (const void*)&k_fused_mh<DT, 8, 4, 2>; break;
+        case 16: fn = (const void*)&k_fused_mh<DT, 16, 4, 2>; break;
+        }
     }
+    if (!fn) return cudaErrorInvalidValue;
     constexpr int U = 4;
     if (a.nchunks <= 0) return cudaSuccess;
     const int64_t groups_per_cta = RING_THREADS / G;
     int64_t blocks = (a.nchunks + groups_per_cta - 1) / groups_per_cta;
     if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;
-    const size_t smem = (size_t)(RING_THREADS / 32) * fused_mh_ring_bytes(U);
+    const size_t smem = (size_t)(RING_THREADS / 32) * fused_mh_ring_bytes(U, NV);
     void* args[] = {(void*)&a};
     return cudaLaunchKernel(fn, dim3((unsigned)blocks, 1), dim3(RING_THREADS), args, smem, s);
 }
 
-cudaError_t launch_fused_mh(int dt, int G, const FusedArgs& a, cudaStream_t s)
+cudaError_t launch_fused_mh_nv(int dt, int G, int NV, const FusedArgs& a, cudaStream_t s)
 {
     switch (dt) {
-    case DT_F32: return launch_fused_mh_t<DT_F32>(G, a, s);
-    case DT_BF16: return launch_fused_mh_t<DT_BF16>(G, a, s);
-    case DT_F16: return launch_fused_mh_t<DT_F16>(G, a, s);
+    case DT_F32: return launch_fused_mh_t<DT_F32>(G, NV, a, s);
+    case DT_BF16: return launch_fused_mh_t<DT_BF16>(G, NV, a, s);
+    case DT_F16: return launch_fused_mh_t<DT_F16>(G, NV, a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_mh(int dt, int G, const FusedArgs& a, cudaStream_t s)
+{
+    return launch_fused_mh_nv(dt, G, 1, a, s);
 }
 
 template <int DT>
