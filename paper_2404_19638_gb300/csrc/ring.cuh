@@ -558,7 +558,11 @@ __device__ __forceinline__ void spmm_ring_span(const SpmmArgs& a, const Group<G>
                     sc[4 * c + 0] = sc[4 * c + 1] = sc[4 * c + 2] = sc[4 * c + 3] = 1.f;
                 }
             }
-            if (eb >= e0 && eb + U <= e1 && rc[U - 1] == cur) {
+            // one fast/general decision for the lane groups running together
+            // (each group walks its own span, so they may have parted): a batch
+            // that could take the fast path is also right on the general one,
+            // and groups running the two paths one after the other cost both
+            if (__all_sync(__activemask(), eb >= e0 && eb + U <= e1 && rc[U - 1] == cur)) {
 #pragma unroll
                 for (int u = 0; u < U; ++u)
 #pragma unroll
