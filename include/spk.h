@@ -203,6 +203,16 @@ spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2,
                      spk_dtype dta, const void* A, int64_t lda, const float* a_scale,
                      spk_dtype dtb, const void* B, int64_t ldb, const float* b_scale,
                      int32_t K, float* out, const spk_tune* tune, void* stream);
+/* SDDMM in heads (equal slices of K, head width K / heads a whole number of
+ * 16-byte vectors): out[h * nnz + e] = vals[e] * <A[i, h*dh:(h+1)*dh],
+ * B[j, h*dh:(h+1)*dh]> (Eq. 1 on each slice; vals NULL = ones, 16-byte
+ * aligned), out FP32 heads x nnz.  A (M x K) and B (N x K) share dtype dt
+ * (F32 or BF16), 16-byte aligned with 16-byte row strides.  One pass over the
+ * pattern for all heads on the balanced schedule (needs spk_schedule_build);
+ * K must fill the default SDDMM lane block (K = 32, 64, 128 in F32; 64, 128
+ * in BF16), else SPK_ERR_UNSUPPORTED (call spk_sddmm per slice then). */
+spk_status spk_sddmm_mh(spk_csr S, const float* vals, int32_t heads, spk_dtype dt, const void* A, int64_t lda,
+                        const void* B, int64_t ldb, int32_t K, float* out, void* stream);
 
 /* SpMM, Eq. 2.  C (M x K, dtype dtc in {F32, BF16, F16}, leading dim ldc)
  * = S B, or C += S B with accumulate = 1.  Empty rows are written as zero

@@ -18,6 +18,7 @@ from __future__ import annotations
 import torch
 
 from . import ops
+from .binding import SpkError
 from .sparse import CSR
 
 
@@ -119,6 +120,12 @@ def gnn_layer(S: CSR, H, vals=None):
     return GNNLayerFunction.apply(S, vals, H)
 
 
+def _dw_per_head(S, dY, B, dw, heads, Kh):
+    for h in range(heads):
+        c0 = h * Kh
+        ops.sddmm(S, dY[:, c0:c0 + Kh], B[:, c0:c0 + Kh], out=dw[h], use_default_vals=False)
+
+
 class FusedMMFunction(torch.autograd.Function):
     """Differentiable FusedMM: per head h, e = scale * s * <A_i, B_j>,
     w = e or its row softmax, Y_i = sum_j w_ij B_j.
@@ -128,7 +135,8 @@ class FusedMMFunction(torch.autograd.Function):
           = <dY_i, Y_i> (read from the saved output)
       c = scale * s * g;  dA = C B;  dB = C^T A + W^T dY  (C, W: S's pattern
       holding c, w)
-    Steps: one SDDMM per head for dw, the row term and score gradient
+    Steps: dw by one multi-head SDDMM (FP32 operands; one SDDMM per head
+    otherwise, or where no multi-head kernel covers K), the row term and score gradient
     kernels (c folds in the sparse values, so every SpMM takes one value
     array per head), then dA = one multi-head SpMM (c per head) and
     dB = two multi-head SpMM^T (c with A, then w with dY added), each one
@@ -155,9 +163,13 @@ class FusedMMFunction(torch.autograd.Function):
         Kh = K // heads
         w = ops.fused_weights(S, scores, lse, heads, softmax) if softmax else scores
         dw = torch.empty_like(scores)
-        for h in range(heads):
-            c0 = h * Kh
-            ops.sddmm(S, dY[:, c0:c0 + Kh], B[:, c0:c0 + Kh], out=dw[h], use_default_vals=False)
+        if B.dtype == torch.float32 and heads > 1:
+            try:                                   # all heads in one pass over the pattern
+                ops.sddmm_mh(S, dY, B, heads, out=dw)
+            except SpkError:
+                _dw_per_head(S, dY, B, dw, heads, Kh)
+        else:
+            _dw_per_head(S, dY, B, dw, heads, Kh)
         R = ops.fused_rowdot(dY, Y, heads) if softmax else None
         c = ops.fused_score_grad(S, w, dw, R, heads, softmax, scale, v)
         dA = dB = None

@@ -73,6 +73,7 @@ _PROTOS = {
     "spk_schedule_bounds": (ctypes.c_int, [_vp, _vp, _vp]),
     "spk_merge_path_points": (ctypes.c_int, [_vp, _i32, _i64, _vp, _vp]),
     "spk_spmm_workspace_size": (ctypes.c_int, [_vp, _i32, _P(_sz)]),
+    "spk_sddmm_mh": (ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "spk_sddmm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _i64, _vp, ctypes.c_int, _vp, _i64, _vp, _i32,
                                  _vp, _P(Tune), _vp]),
     "spk_spmm": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _i64, _vp, _i32, ctypes.c_int, _vp, _i64, _i32,

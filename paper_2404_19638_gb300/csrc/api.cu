@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "fused.cuh"
+#include "heads.cuh"
 
 namespace spk {
 
@@ -481,6 +482,48 @@ extern "C" spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2
     a.nchunks = S->nchunks;
     cudaError_t e = launch_sddmm(dta, dtb, L, a, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "spk_sddmm launch");
+    return SPK_OK;
+}
+
+// Several heads (equal slices of K): out[h * nnz + e] = s_e * <A[i, head h], B[j, head h]>.
+extern "C" spk_status spk_sddmm_mh(spk_csr S, const float* vals, int32_t heads, spk_dtype dt, const void* A,
+                                   int64_t lda, const void* B, int64_t ldb, int32_t K, float* out, void* stream)
+{
+    REQUIRE(S, SPK_ERR_ARG, "spk_sddmm_mh: S is NULL");
+    REQUIRE(dt == SPK_F32 || dt == SPK_BF16, SPK_ERR_DTYPE, "spk_sddmm_mh: dtype must be F32 or BF16");
+    REQUIRE(K >= 1 && heads >= 1 && K % heads == 0, SPK_ERR_SHAPE,
+            "spk_sddmm_mh: K (%d) must be a positive multiple of heads (%d)", K, heads);
+    REQUIRE(lda >= K && ldb >= K, SPK_ERR_SHAPE, "spk_sddmm_mh: leading dimensions must be >= K");
+    REQUIRE(S->nnz == 0 || (A && B && out), SPK_ERR_ARG, "spk_sddmm_mh: NULL operand");
+    REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_sddmm_mh: pattern belongs to a transpose plan");
+    REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_sddmm_mh: needs spk_schedule_build first");
+    const int vecn = vec_elems(dt);
+    REQUIRE(aligned16(A) && aligned16(B) && (lda * dt_bytes(dt)) % 16 == 0 && (ldb * dt_bytes(dt)) % 16 == 0 &&
+                (!vals || aligned16(vals)),
+            SPK_ERR_SHAPE, "spk_sddmm_mh: A, B (and vals) must be 16-byte aligned with 16-byte row strides");
+    REQUIRE((K / heads) % vecn == 0, SPK_ERR_UNSUPPORTED,
+            "spk_sddmm_mh: a head of %d elements is not a whole number of 16-byte vectors", K / heads);
+    const int nv = K / vecn, nh = nv / heads;
+    int G, NV, U;
+    default_shape(OP_SDDMM, nv, &G, &NV, &U);
+    REQUIRE(heads > 1 || nv == G * NV, SPK_ERR_UNSUPPORTED, "spk_sddmm_mh: K = %d has no whole lane block", K);
+    REQUIRE(heads == 1 || (nv == G * NV && sddmm_mh_supported(dt, G, NV, U, nh)), SPK_ERR_UNSUPPORTED,
+            "spk_sddmm_mh: no kernel for K = %d in %d heads (rows of %d vectors over %d lanes x %d)", K, heads, nv, G,
+            NV);
+    if (S->nnz == 0) return SPK_OK;
+    if (heads == 1)
+        return spk_sddmm(S, vals, nullptr, dt, A, lda, nullptr, dt, B, ldb, nullptr, K, out, nullptr, stream);
+    SddmmArgs a;
+    a.M = S->M; a.N = S->N; a.nnz = S->nnz; a.K = K;
+    a.rowptr = S->rowptr; a.colidx = S->colidx; a.rowidx = S->rowidx;
+    a.vals = vals; a.vals2 = nullptr;
+    a.A = A; a.lda = lda; a.a_scale = nullptr;
+    a.B = B; a.ldb = ldb; a.b_scale = nullptr;
+    a.out = out;
+    a.bnd = S->bnd;
+    a.nchunks = S->nchunks;
+    cudaError_t e = launch_sddmm_mh(dt, G, NV, U, nh, a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spk_sddmm_mh launch");
     return SPK_OK;
 }
 

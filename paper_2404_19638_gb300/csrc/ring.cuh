@@ -153,9 +153,13 @@ template <> struct ASlice<DT_F16> : ASlice16<DT_F16> {};
 // general path: the first new row's A slice arrives through the ring, a
 // second new row inside the same batch is read directly.
 // ----------------------------------------------------------------------------
-template <int DT, int G, int NV, int U, int D, bool ALLV>
+// NH > 0: several heads, each a block of NH consecutive 16-byte vectors of a
+// row (so lane gl's vector t belongs to head (t * G + gl) / NH), one output
+// array of nnz values per head (out + head * nnz); NH = 0: one dot per nonzero.
+template <int DT, int G, int NV, int U, int D, bool ALLV, int NH = 0>
 __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, unsigned char* wsm, int e0, int e1)
 {
+    static_assert(NH == 0 || (G % NH == 0 && (U * NV) % NH == 0), "heads must tile the lanes and the batch");
     constexpr int VECN = vec_elems(DT);
     constexpr int GPW = 32 / G;
     constexpr int WB = GPW * U;
@@ -286,7 +290,8 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
         const int eg = tb0 + b * WB + grp * U;
         const int meta = mmeta[d * GPW + grp];
         const uint4* sB = ringB + d * U * NV * 32 + lane;
-        float p[U];
+        constexpr int V = NH ? U * NV : U;               // partial dots this lane reduces
+        float p[V];
         if (meta & 1) {                                  // issued on the fast path (a warp-wide decision)
             if (meta & 2) {                              // new row from nonzero 0 on: its A slice is in the ring
 #pragma unroll
@@ -295,18 +300,28 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                float2 acc = make_float2(0.f, 0.f);
+                if constexpr (NH == 0) {
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < NV; ++t)
-                    if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
-                p[u] = acc.x + acc.y;
+                    for (int t = 0; t < NV; ++t)
+                        if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
+                    p[u] = acc.x + acc.y;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
+                        p[u * NV + t] = acc.x + acc.y;
+                    }
+                }
             }
         } else {
             const int m = meta >> 1;
             const int ua = m ? __ffs(m) - 1 : U;
 #pragma unroll
+            for (int k = 0; k < V; ++k) p[k] = 0.f;
+#pragma unroll
             for (int u = 0; u < U; ++u) {
-                p[u] = 0.f;
                 const int e = eg + u;
                 if (e < e0 || e >= e1) continue;
                 if ((m >> u) & 1) {
@@ -323,12 +338,51 @@ __device__ __forceinline__ void sddmm_ring_span(const SddmmArgs& a, int lane, un
                             if (vin[t]) av[t].set(__ldg(arow + t * G));
                     }
                 }
-                float2 acc = make_float2(0.f, 0.f);
+                if constexpr (NH == 0) {
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t < NV; ++t)
-                    if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
-                p[u] = acc.x + acc.y;
+                    for (int t = 0; t < NV; ++t)
+                        if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
+                    p[u] = acc.x + acc.y;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NV; ++t) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        if (vin[t]) av[t].dot(acc, sB[(u * NV + t) * 32]);
+                        p[u * NV + t] = acc.x + acc.y;
+                    }
+                }
             }
+        }
+        if constexpr (NH > 0) {
+            // Recursive halving over the NH lanes of a head block: after
+            // log2(NH) levels lane gl holds C = V / NH finished dots, those of
+            // values C * (gl % NH) + i, value k = u * NV + t being nonzero eg + u
+            // against vector t of its row, which belongs to head
+            // (t * G + gl) / NH = t * (G / NH) + gl / NH.
+            constexpr int C = V / NH;
+#pragma unroll
+            for (int dd = NH / 2, half = V / 2; dd >= 1; dd >>= 1, half >>= 1) {
+                const bool upper = (gl & dd) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    const float send = upper ? p[i] : p[i + half];
+                    const float keep = upper ? p[i + half] : p[i];
+                    p[i] = keep + __shfl_xor_sync(gmask, send, dd, G);
+                }
+            }
+            const int kb0 = C * (gl % NH);
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const int k = kb0 + i, u = k / NV, t = k % NV;
+                const int ew = eg + u;
+                if (ew < e0 || ew >= e1) continue;
+                float sv = vals ? mval[d * WB + grp * U + u] : 1.f;
+                if (vals2) sv *= mval2[d * WB + grp * U + u];
+                const int head = t * (G / NH) + gl / NH;
+                __stcs(a.out + (int64_t)head * a.nnz + ew, sv * p[i]);
+            }
+            continue;
         }
         // Reduce-scatter over the low log2(U) lane bits, then butterflies over
         // the remaining G/U lane subsets: nonzero eg + (gl % U) ends in lane gl.

@@ -74,6 +74,28 @@ def sddmm(S: CSR, A: torch.Tensor, B: torch.Tensor, vals=None, vals2=None, *, a_
     return out
 
 
+def sddmm_mh(S: CSR, A: torch.Tensor, B: torch.Tensor, heads: int, vals=None, *,
+             out: torch.Tensor | None = None) -> torch.Tensor:
+    """Per head h (equal slices of K): out[h, e] = s_e * <A[i, head h], B[j, head h]>,
+    heads x nnz FP32, one pass over the pattern for all heads (vals None: ones).
+    Raises SpkError where no multi-head kernel covers K (use sddmm per slice)."""
+    dta, lda = _dense(A, "A", S.device)
+    dtb, ldb = _dense(B, "B", S.device)
+    if dta != dtb:
+        raise TypeError("A and B must have the same dtype")
+    if A.size(0) != S.M or B.size(0) != S.N or A.size(1) != B.size(1):
+        raise ValueError("A must be M x K and B N x K")
+    K = A.size(1)
+    if out is None:
+        out = torch.empty((heads, S.nnz), dtype=torch.float32, device=S.device)
+    if out.dtype != torch.float32 or tuple(out.shape) != (heads, S.nnz) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous heads x nnz float32 tensor")
+    vals = _vals(vals, S, "vals")
+    check(lib().spk_sddmm_mh(S.handle, _ptr(vals), int(heads), dta, A.data_ptr(), lda, B.data_ptr(), ldb, K,
+                             out.data_ptr(), _stream(S.device)), "spk_sddmm_mh")
+    return out
+
+
 def spmm(S: CSR, B: torch.Tensor, vals=None, vals2=None, *, b_scale=None, out: torch.Tensor | None = None,
          out_dtype=torch.float32, accumulate: bool = False, tune=None, use_default_vals: bool = True) -> torch.Tensor:
     """C = S B (or C += S B with accumulate=True).  C is M x K."""

@@ -219,3 +219,40 @@ def test_multi_head_spmm_and_spmm_t(spk, heads, K, dt):
     acc = base.clone()
     spk.ops.spmm_mh(S, tB, tV, heads, out=acc, accumulate=True)
     np.testing.assert_allclose(acc.cpu().numpy(), base.cpu().numpy() + C, rtol=1e-6, atol=1e-5)
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("K,heads", [(64, 2), (64, 4), (64, 8), (128, 4), (32, 2), (128, 8)])
+def test_sddmm_heads_one_pass(spk, dt, K, heads):
+    """SDDMM in heads (spk_sddmm_mh): each head's slice against the oracle's
+    SDDMM of that slice at the component-wise gate, with and without values,
+    split rows included; where no multi-head kernel covers K the call is
+    refused with SpkError and nothing else."""
+    from paper_2404_19638_gb300 import ops
+    rp, ci = edge_pattern(700, 600, 5 * K + heads, long_row=2500)
+    g = np.random.default_rng(K + heads)
+    vals = g.uniform(-1, 1, ci.size).astype(np.float32)
+    S = spk.CSR(rp, ci, (700, 600), torch.from_numpy(vals), device=DEV, chunk_work=64)
+    A = torch.from_numpy(g.standard_normal((700, K)).astype(np.float32)).to(DEV)
+    B = torch.from_numpy(g.standard_normal((600, K)).astype(np.float32)).to(DEV)
+    fmt = None
+    if dt == torch.bfloat16:
+        A, B = spk.cast(A, dt), spk.cast(B, dt)
+        fmt = "bf16"
+    Aq = A.float().cpu().numpy() if fmt is None else A.view(torch.int16).cpu().numpy().view(np.uint16)
+    Bq = B.float().cpu().numpy() if fmt is None else B.view(torch.int16).cpu().numpy().view(np.uint16)
+    vecn = 4 if dt == torch.float32 else 8
+    covered = (dt == torch.float32 and K in (32, 64, 128)) or (dt == torch.bfloat16 and K in (64, 128))
+    if not covered or (K // heads) % vecn:
+        with pytest.raises(spk.SpkError):
+            ops.sddmm_mh(S, A, B, heads)
+        return
+    dh = K // heads
+    for v in (None, S.vals):
+        got = ops.sddmm_mh(S, A, B, heads, vals=v).cpu().numpy()
+        vv = None if v is None else vals
+        for h in range(heads):
+            ref = oracle.sddmm(rp, ci, Aq[:, h * dh:(h + 1) * dh], Bq[:, h * dh:(h + 1) * dh], vv, fmt_a=fmt, fmt_b=fmt)
+            den = oracle.sddmm(rp, ci, Aq[:, h * dh:(h + 1) * dh], Bq[:, h * dh:(h + 1) * dh], vv, fmt_a=fmt,
+                               fmt_b=fmt, absmode=True)
+            assert comp_err(got[h], ref, den) <= TOL, (K, heads, h)
