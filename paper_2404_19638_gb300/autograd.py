@@ -166,7 +166,9 @@ class FusedMMFunction(torch.autograd.Function):
         if B.dtype == torch.float32 and heads > 1:
             try:                                   # all heads in one pass over the pattern
                 ops.sddmm_mh(S, dY, B, heads, out=dw)
-            except SpkError:
+            except SpkError as err:                # no multi-head kernel for this K: one SDDMM per head
+                if err.code != "SPK_ERR_UNSUPPORTED":
+                    raise
                 _dw_per_head(S, dY, B, dw, heads, Kh)
         else:
             _dw_per_head(S, dY, B, dw, heads, Kh)
