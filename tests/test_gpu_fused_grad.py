@@ -120,8 +120,10 @@ def test_score_grad_kernel(spk, softmax):
         assert comp_err(de, ref, den) <= TOL
 
 
-@pytest.mark.parametrize("heads,softmax", [(1, False), (1, True), (2, True), (4, True), (4, False)])
+@pytest.mark.parametrize("heads,softmax", [(1, False), (1, True), (2, True), (4, True), (4, False), (3, True)])
 def test_fusedmm_grad_f32(spk, heads, softmax):
+    # heads 2 and 4 take the multi-head dw SDDMM; 3 heads (K = 48) have no
+    # multi-head kernel and take one SDDMM per head
     M, N, K = 600, 450, 16 * heads
     rp, ci, vals, A, B, dY = _case(M, N, K, seed=10 + heads + 5 * softmax)
     scale = 1.0 / np.sqrt(K // heads)
