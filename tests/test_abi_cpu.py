@@ -148,3 +148,29 @@ def test_python_wrappers_reject_host_tensors():
         ops.cast(X, torch.bfloat16)
     with pytest.raises(TypeError):
         ops.quantize_e4m3_rows(X)
+
+
+def test_batch_shape_lists_and_register_choice(L):
+    """The batched shapes per op (host only) and the register-budget call's
+    argument checks."""
+    from paper_2404_19638_gb300.binding import batch_shapes
+    sd, sp = batch_shapes(0), batch_shapes(1)
+    assert sd and sp and batch_shapes(2) == []
+    assert all(U in (4, 8) and G in (4, 8, 16) and NV == 1 for G, NV, U in sd + sp)
+    assert set(sd) <= set(sp)                                             # SpMM adds 8-nonzero batches
+    assert any(U == 8 for _, _, U in sp)
+    buf = (ctypes.c_int32 * 3)()
+    assert L.spk_batch_shapes(1, buf, 1) == len(sp) and tuple(buf) == sp[0]
+    assert L.spk_batch_set_registers(None, 80) == 1                      # NULL handle
+
+
+def test_sddmm_heads_rejects_bad_arguments(L):
+    """spk_sddmm_mh checks its arguments on the host before any launch."""
+    h = _handle(L)
+    mh = lambda heads, dt, K, lda=64, ldb=64: L.spk_sddmm_mh(h, None, heads, dt, 4096, lda, 8192, ldb, K, 12288, None)
+    assert mh(4, 2, 64) == 4                                             # F16 not offered
+    assert mh(3, 0, 64) == 2                                             # K not a multiple of heads
+    assert mh(4, 0, 64, lda=32) == 2                                     # leading dimension < K
+    assert mh(4, 0, 64) == 9                                             # no schedule attached
+    assert L.spk_sddmm_mh(None, None, 4, 0, 4096, 64, 8192, 64, 64, 12288, None) == 1
+    L.spk_csr_destroy(h)
