@@ -258,9 +258,8 @@ spk_status spk_spmm_mh(spk_csr S, const float* vals, int64_t hstride, int32_t he
  *    no scratch and have no limit.
  *  - Set-up: the first call in a CUDA context of a device (the current one)
  *    looks up the scratch's device address with cudaGetSymbolAddress and
- *    keeps it for that context; make that first call before any stream
- *    capture.  cudaDeviceReset ends the context, so the first call after it
- *    looks the address up again (and again belongs before any capture).
+ *    keeps it for that context.  cudaDeviceReset ends the context, so the
+ *    first call after it looks the address up again.
  *  - Sharing: every call on a device uses the same scratch, which keeps the
  *    last call's contents.  Nothing in it needs to start at zero, so it is
  *    never cleared.  Calls that overlap on the GPU (other streams, other host
