@@ -86,17 +86,26 @@ def test_fused_head_per_grid_row(spk, shape):
                tune={"group_lanes": G, "vecs_per_lane": NV, "unroll": U})
 
 
-@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16])
-@pytest.mark.parametrize("nv_lane", [1, 2])
-@pytest.mark.parametrize("K,heads", [(32, 1), (64, 2), (64, 4), (128, 4)])
+def _lane_splits():
+    """(dtype, vectors a lane, K, heads) whose rows split into a compiled lane
+    width: 4-32 lanes (at most 16 with two vectors a lane), whole heads per lane."""
+    out = []
+    for dt in (torch.float32, torch.bfloat16):
+        vecn = 4 if dt == torch.float32 else 8
+        for nv_lane in (1, 2):
+            for K, heads in ((32, 1), (64, 2), (64, 4), (128, 4)):
+                nv = K // vecn
+                G = nv // nv_lane
+                if nv % nv_lane == 0 and G in (4, 8, 16, 32) and not (nv_lane == 2 and G == 32) and G % heads == 0:
+                    name = f"{'f32' if dt == torch.float32 else 'bf16'}-nv{nv_lane}-K{K}-h{heads}"
+                    out.append(pytest.param(dt, nv_lane, K, heads, id=name))
+    return out
+
+
+@pytest.mark.parametrize("dt,nv_lane,K,heads", _lane_splits())
 def test_fused_all_heads_vectors_per_lane(spk, dt, nv_lane, K, heads):
     """The all-heads kernel with one or two adjacent 16-byte vectors a lane
     (tune.vecs_per_lane alone), with and without softmax, split rows included."""
-    vecn = 4 if dt == torch.float32 else 8
-    nv = K // vecn
-    G = nv // nv_lane
-    if nv % nv_lane or G not in (4, 8, 16, 32) or (nv_lane == 2 and G == 32) or G % heads:
-        pytest.skip("shape does not split into lanes of this width")
     rp, ci, vals, A, B = _case(500, 420, K, seed=5 * K + heads + nv_lane)
     for softmax in (False, True):
         _check(spk, rp, ci, vals, A, B, heads, softmax, dt, W=64, tune={"vecs_per_lane": nv_lane})
