@@ -27,7 +27,8 @@
  *    independent entries.  Values are passed per call (the pattern stays fixed
  *    while values change, Sec. 5.1), as FP32 `vals` (NULL = all ones) times an
  *    optional second FP32 factor `vals2` (NULL = ones), indexed like colidx.
- *  - Dense matrices are row-major with a leading dimension (elements) >= K.
+ *  - Dense matrices are row-major with a leading dimension (elements) >= K;
+ *    the inputs' row strides must stay below 4 GiB (SPK_ERR_SHAPE otherwise).
  *  - Arithmetic: inputs are widened to FP32 and accumulated in FP32 (no FP64
  *    on the GPU).  E4M3 operands carry one FP32 scale per row: the value of an
  *    element is code * scale[row].
@@ -48,7 +49,7 @@ extern "C" {
 typedef enum spk_status {
     SPK_OK = 0,
     SPK_ERR_ARG = 1,          /* null pointer, negative size, bad flag            */
-    SPK_ERR_SHAPE = 2,        /* leading dimension < K, K < 1, size mismatch      */
+    SPK_ERR_SHAPE = 2,        /* leading dimension < K or too large, K < 1, size mismatch */
     SPK_ERR_INDEX = 3,        /* malformed CSR found by spk_csr_validate          */
     SPK_ERR_DTYPE = 4,        /* unsupported dtype or dtype combination           */
     SPK_ERR_WORKSPACE = 5,    /* caller buffer too small or misaligned            */

@@ -84,6 +84,9 @@ static spk_status cuda_fail(cudaError_t e, const char* where)
     } while (0)
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+// The gather kernels form a row's address as row x (row stride in bytes) with
+// the stride held in 32 bits: a row stride must stay below 4 GiB.
+static bool stride32(int64_t ld, int dt) { return ld <= (int64_t)0xFFFFFFFFu / dt_bytes(dt); }
 static bool valid_dt(int dt) { return dt >= SPK_F32 && dt <= SPK_E4M3; }
 
 extern "C" const char* spk_status_string(spk_status s)
@@ -461,6 +464,7 @@ extern "C" spk_status spk_sddmm(spk_csr S, const float* vals, const float* vals2
             "spk_sddmm: dtype pair (%d, %d) not supported", (int)dta, (int)dtb);
     REQUIRE(K >= 1, SPK_ERR_SHAPE, "spk_sddmm: K must be >= 1 (got %d)", K);
     REQUIRE(lda >= K && ldb >= K, SPK_ERR_SHAPE, "spk_sddmm: leading dimensions must be >= K");
+    REQUIRE(stride32(lda, dta) && stride32(ldb, dtb), SPK_ERR_SHAPE, "spk_sddmm: row strides must be below 4 GiB");
     REQUIRE(S->nnz == 0 || (A && B && out), SPK_ERR_ARG, "spk_sddmm: NULL operand");
     REQUIRE(dta != SPK_E4M3 || (a_scale && b_scale), SPK_ERR_ARG, "spk_sddmm: E4M3 needs a_scale and b_scale");
     REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_sddmm: pattern belongs to a transpose plan");
@@ -494,6 +498,7 @@ extern "C" spk_status spk_sddmm_mh(spk_csr S, const float* vals, int32_t heads, 
     REQUIRE(K >= 1 && heads >= 1 && K % heads == 0, SPK_ERR_SHAPE,
             "spk_sddmm_mh: K (%d) must be a positive multiple of heads (%d)", K, heads);
     REQUIRE(lda >= K && ldb >= K, SPK_ERR_SHAPE, "spk_sddmm_mh: leading dimensions must be >= K");
+    REQUIRE(stride32(lda, dt) && stride32(ldb, dt), SPK_ERR_SHAPE, "spk_sddmm_mh: row strides must be below 4 GiB");
     REQUIRE(S->nnz == 0 || (A && B && out), SPK_ERR_ARG, "spk_sddmm_mh: NULL operand");
     REQUIRE(!S->vperm, SPK_ERR_ARG, "spk_sddmm_mh: pattern belongs to a transpose plan");
     REQUIRE(S->has_sched, SPK_ERR_STATE, "spk_sddmm_mh: needs spk_schedule_build first");
@@ -548,6 +553,7 @@ static spk_status spmm_common(const char* name, const spk_csr_s* S, const float*
             "%s: output dtype must be F32, BF16 or F16", name);
     REQUIRE(K >= 1, SPK_ERR_SHAPE, "%s: K must be >= 1 (got %d)", name, K);
     REQUIRE(ldb >= K && ldc >= K, SPK_ERR_SHAPE, "%s: leading dimensions must be >= K", name);
+    REQUIRE(stride32(ldb, dtb), SPK_ERR_SHAPE, "%s: the row stride of the dense input must be below 4 GiB", name);
     REQUIRE(accumulate == 0 || accumulate == 1, SPK_ERR_ARG, "%s: accumulate must be 0 or 1", name);
     REQUIRE(S->M == 0 || C, SPK_ERR_ARG, "%s: output is NULL", name);
     REQUIRE(S->nnz == 0 || B, SPK_ERR_ARG, "%s: dense input is NULL", name);
@@ -656,6 +662,7 @@ extern "C" spk_status spk_fusedmm(spk_csr S, const float* vals, float scale, int
     REQUIRE(dh % vecn == 0, SPK_ERR_UNSUPPORTED, "spk_fusedmm: head width %d is not a multiple of %d elements", dh,
             vecn);
     REQUIRE(lda >= K && ldb >= K && ldy >= K, SPK_ERR_SHAPE, "spk_fusedmm: leading dimensions must be >= K");
+    REQUIRE(stride32(lda, dt) && stride32(ldb, dt), SPK_ERR_SHAPE, "spk_fusedmm: row strides must be below 4 GiB");
     REQUIRE(S->nnz == 0 || (A && B), SPK_ERR_ARG, "spk_fusedmm: NULL operand");
     REQUIRE(S->M == 0 || Y, SPK_ERR_ARG, "spk_fusedmm: Y is NULL");
     REQUIRE(aligned16(A) && aligned16(B) && aligned16(Y) && (lda * dt_bytes(dt)) % 16 == 0 &&

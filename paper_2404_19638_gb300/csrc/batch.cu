@@ -206,6 +206,10 @@ static spk_status plan_batch(const spk_batch_item* items, int32_t count, BatchPl
         if (it.K % vecn) return bfail(SPK_ERR_UNSUPPORTED, where + "K must be a multiple of 16 bytes of elements");
         if (it.ldb < it.K || (it.ldb * dt_bytes(it.dt)) % 16 || (reinterpret_cast<uintptr_t>(it.B) & 15))
             return bfail(SPK_ERR_SHAPE, where + "B must be 16-byte aligned with ldb >= K");
+        // row addresses are formed with 32-bit byte strides
+        const int64_t max_ld = (int64_t)0xFFFFFFFFu / dt_bytes(it.dt);
+        if (it.ldb > max_ld || (it.op == 0 && it.lda > max_ld))
+            return bfail(SPK_ERR_SHAPE, where + "row strides must be below 4 GiB");
         if (S->nnz > 0 && !it.B) return bfail(SPK_ERR_ARG, where + "B is NULL");
         if (!it.out && (it.op == 1 ? S->M > 0 : S->nnz > 0)) return bfail(SPK_ERR_ARG, where + "out is NULL");
         if (it.op == 0) {

@@ -63,6 +63,10 @@ def test_compute_calls_reject_bad_arguments(L):
     assert sddmm(1, 4096, 16, None, 0, 4096, 16, None, 16, 4096, None, None) == 4
     assert sddmm(0, 4096, 16, None, 0, 4096, 16, None, 0, 4096, None, None) == 2
     assert sddmm(0, 4096, 8, None, 0, 4096, 16, None, 16, 4096, None, None) == 2
+    big = 1 << 30                                                           # rows of 4 GiB in FP32
+    assert sddmm(0, 4096, 16, None, 0, 4096, big, None, 16, 4096, None, None) == 2
+    assert sddmm(0, 4096, big, None, 0, 4096, 16, None, 16, 4096, None, None) == 2
+    assert b"4 GiB" in L.spk_last_error()
     assert sddmm(3, 4096, 16, None, 3, 4096, 16, None, 16, 4096, None, None) == 1
     assert sddmm(0, None, 16, None, 0, 4096, 16, None, 16, 4096, None, None) == 1
     # balanced variant without a schedule
@@ -75,6 +79,7 @@ def test_compute_calls_reject_bad_arguments(L):
     assert spmm(0, 4096, 16, None, 16, 3, 8192, 16, 0, None, 0, None, None) == 4     # E4M3 output
     assert spmm(0, 4096, 16, None, 16, 0, 8192, 16, 2, None, 0, None, None) == 1     # accumulate flag
     assert spmm(0, 4096, 16, None, 16, 0, 8192, 8, 0, None, 0, None, None) == 2      # ldc < K
+    assert spmm(0, 4096, 1 << 30, None, 16, 0, 8192, 16, 0, None, 0, None, None) == 2  # 4 GiB rows of B
     assert spmm(0, 4096, 16, None, 16, 0, None, 16, 0, None, 0, None, None) == 1     # C NULL
     assert L.spk_spmm(None, None, None, 0, 4096, 16, None, 16, 0, 8192, 16, 0, None, 0, None, None) == 1
     L.spk_csr_destroy(h)
@@ -171,6 +176,7 @@ def test_sddmm_heads_rejects_bad_arguments(L):
     assert mh(4, 2, 64) == 4                                             # F16 not offered
     assert mh(3, 0, 64) == 2                                             # K not a multiple of heads
     assert mh(4, 0, 64, lda=32) == 2                                     # leading dimension < K
+    assert mh(4, 0, 64, ldb=1 << 30) == 2                                # rows of 4 GiB
     assert mh(4, 0, 64) == 9                                             # no schedule attached
     assert L.spk_sddmm_mh(None, None, 4, 0, 4096, 64, 8192, 64, 64, 12288, None) == 1
     L.spk_csr_destroy(h)
